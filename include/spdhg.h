@@ -1,0 +1,195 @@
+/*
+ * spdhg.h -- C ABI of the GB300 SPDHG+ PET reconstruction library (libspdhg.so).
+ *
+ * Method: Ehrhardt, Markiewicz, Schoenlieb, "Faster PET reconstruction with non-smooth priors
+ * by randomization and preconditioning".  The library solves
+ *     min_{u >= 0}  sum_i D_i(P_i u) + alpha R(u)                 (Sec. 2.1, Problem "PET
+ *                                                                    Reconstruction with Subsets")
+ * with SPDHG (Algorithm 2), preconditioned step sizes (Eq. EQU:STEPSIZE:PRECOND) and balanced
+ * sampling (Sec. 4.2).  All arithmetic runs in the library's CUDA kernels on the current device.
+ *
+ * Conventions
+ *   image     x[iy][ix][iz], z fastest; voxel (ix,iy,iz) = [X_ix, X_ix+1) x [Y_iy, Y_iy+1) x
+ *             [Z_iz, Z_iz+1), X_i = -nx*vx/2 + i*vx (same for y, z); float32.
+ *   sinogram  y[view][radial][plane], plane fastest; float32.  View v has angle v*pi/n_views,
+ *             radial bin r sits at s = (r - (n_radial-1)/2) * d_radial.
+ *   planes    grouped in segments (fixed axial tilt); plane q of segment g has its LOR mid-point
+ *             at z = seg_zmid0[g] + q*seg_dzmid[g] and its two ends seg_dz[g] apart axially.
+ *   LOR       P(t) = (s cos - t sin, s sin + t cos, z_mid + t dz/(2h)), t in [-h, h],
+ *             h = sqrt(radius^2 - s^2): the chord between two points of the detector cylinder.
+ *   projector (L x)_j = sum_k |LOR_j intersect voxel_k| x_k, lengths in units of vx; a line lying
+ *             in a grid plane belongs to the voxel whose lower face holds it.  P = diag(mult) L
+ *             ("P performs the projection and includes geometric factors, attenuation and
+ *             normalization", Sec. 1.2).
+ *   subsets   view-interleaved: subset i = views v with v mod n_subsets == i ("subsets with
+ *             equidistantly divided angles", Sec. 4).
+ *   blocks    SPDHG block indices 0..m-1 are the data subsets; m (and m+1 for TGV) the prior.
+ *
+ * Errors: every call returns SPDHG_OK (0) or a negative spdhg_status; no call aborts the process.
+ * The message of the last failure on a context is available from spdhg_last_error().  CUDA
+ * errors raised by a kernel launched through a context are reported as SPDHG_ERR_CUDA.
+ * Ownership: the context owns every buffer it allocates (released by spdhg_destroy); the caller
+ * owns every pointer it passes and the library keeps none of them after the call returns.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream); kernels of a call are
+ * enqueued on it in order, and calls that return data to host memory synchronise it.
+ */
+#ifndef SPDHG_H
+#define SPDHG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spdhg_ctx spdhg_ctx;
+
+typedef enum {
+  SPDHG_OK = 0,
+  SPDHG_ERR_ARG = -1,         /* invalid argument (null pointer, out-of-range index, bad size) */
+  SPDHG_ERR_CUDA = -2,        /* a CUDA runtime call or kernel failed */
+  SPDHG_ERR_OOM = -3,         /* device allocation failed */
+  SPDHG_ERR_DATA = -4,        /* non-finite or negative data, non-positive multiplier */
+  SPDHG_ERR_TIMEOUT = -5,     /* a bounded device-side wait expired */
+  SPDHG_ERR_DIVERGED = -6,    /* the FP64 objective became non-finite */
+  SPDHG_ERR_STATE = -7,       /* call order violated (e.g. iterate before setup) */
+  SPDHG_ERR_UNSUPPORTED = -8  /* geometry outside what the kernels handle (see spdhg_create) */
+} spdhg_status;
+
+enum { SPDHG_WHERE_HOST = 0, SPDHG_WHERE_DEVICE = 1 };
+
+/* Scanner + image description.  Arrays are read during spdhg_create only. */
+typedef struct {
+  int nx, ny, nz;             /* image size in voxels */
+  double vx, vy, vz;          /* voxel size in mm; vx == vy is required */
+  int n_radial;               /* radial bins per view */
+  double d_radial;            /* radial bin spacing, mm */
+  int n_views;                /* views over [0, pi) */
+  double radius;              /* detector cylinder radius, mm; > max |s| */
+  int n_segments;
+  const int* seg_n;           /* planes per segment (sinogram plane order is segment-major) */
+  const double* seg_zmid0;    /* LOR mid-point z of the segment's first plane, mm */
+  const double* seg_dzmid;    /* plane spacing within the segment; must equal vz if seg_n > 1 */
+  const double* seg_dz;       /* axial separation z2 - z1 of the segment's LOR ends, mm */
+  int n_subsets;              /* m, number of view-interleaved data subsets */
+} spdhg_geometry;
+
+enum { SPDHG_PRIOR_NONE = 0, SPDHG_PRIOR_TV = 1, SPDHG_PRIOR_DTV = 2, SPDHG_PRIOR_ATV = 3,
+       SPDHG_PRIOR_TGV = 4 };
+enum { SPDHG_SAMPLING_BALANCED = 0, SPDHG_SAMPLING_UNIFORM = 1 };
+
+typedef struct {
+  int prior;                  /* SPDHG_PRIOR_* */
+  double alpha;               /* weight of TV (Eq. EQU:SETTING:TV), dTV, aTV */
+  double alpha0, alpha1;      /* TGV: alpha0 ||grad u - w|| + alpha1 ||E w|| (Sec. 4.3) */
+  double dtv_gamma;           /* dTV: D = I - dtv_gamma xi xi^T, 0 <= dtv_gamma < 1 */
+  double dtv_eta_frac;        /* dTV: xi = grad v / sqrt(|grad v|^2 + eta^2), eta = frac*max|grad v| */
+  int sampling;               /* SPDHG_SAMPLING_*: balanced = prior w.p. 1/2 (Sec. 4.2) */
+  int precond;                /* 1: Eq. EQU:STEPSIZE:PRECOND for data blocks; 0: scalar Eq.
+                                 EQU:STEPSIZE:SCALAR with ||P_i|| by power iteration */
+  double rho;                 /* < 1 (Theorem "Step Size Parameters"); 0.99 if <= 0 */
+  double gamma;               /* > 0; 1 if <= 0 (Sec. 4: gamma = 1) */
+  uint64_t seed;              /* sampler seed (spdhg_run) */
+  int epochs;                 /* spdhg_run: number of epochs */
+  int objective_every;        /* spdhg_run: evaluate Psi every k epochs (0: never) */
+} spdhg_params;
+
+typedef struct {
+  int epochs_done;
+  int64_t iterations_done;
+  double* objective;          /* caller array of epochs+1 doubles or NULL: Psi after each
+                                 evaluated epoch (index 0 = start), NaN where not evaluated */
+  double* epoch_ms;           /* caller array of `epochs` doubles or NULL: device time per epoch */
+} spdhg_report;
+
+/* Creates a context for a geometry on the current CUDA device (device tables, no data yet).
+ * Fails with SPDHG_ERR_UNSUPPORTED when vx != vy, when a multi-plane segment's spacing differs
+ * from vz, when radius <= max |s|, or when an oblique LOR crosses more than 4 slices inside one
+ * transaxial pixel.  *out receives the context (NULL on failure). */
+int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out);
+
+/* Releases every device buffer of the context.  NULL is accepted. */
+void spdhg_destroy(spdhg_ctx* ctx);
+
+/* Message of the last failure on ctx (empty string if none); valid until the next call on ctx. */
+const char* spdhg_last_error(const spdhg_ctx* ctx);
+
+/* Sizes: voxels N, bins M, SPDHG blocks n for the current parameters (m before spdhg_setup). */
+int spdhg_sizes(const spdhg_ctx* ctx, int64_t* n_voxels, int64_t* n_bins, int* n_blocks);
+
+/* Copies the measured counts b (Sec. 1.2: b in N^M), the background r (scatter + randoms) and
+ * the per-bin multipliers mult (attenuation x normalisation; NULL = all ones) into the context;
+ * side is the anatomical side image of dTV (N voxels; NULL unless dTV is used).  where =
+ * SPDHG_WHERE_HOST or SPDHG_WHERE_DEVICE for all four pointers.  Rejects (SPDHG_ERR_DATA)
+ * non-finite values, b < 0, r < 0, mult <= 0. */
+int spdhg_set_data(spdhg_ctx* ctx, const float* b, const float* r, const float* mult,
+                   const float* side, int where);
+
+/* y = P_i x on the bins of subset i (i = -1: all bins); bins of other subsets are not written.
+ * x (N floats) and y (M floats) are device pointers in the documented layouts.  Uses mult of the
+ * last spdhg_set_data (ones if none). */
+int spdhg_project(spdhg_ctx* ctx, const float* x, float* y, int subset, void* stream);
+
+/* x = P_i^T y restricted to the bins of subset i (i = -1: all bins); device pointers. */
+int spdhg_backproject(spdhg_ctx* ctx, const float* y, float* x, int subset, void* stream);
+
+/* Step sizes and initial state for `params`: sigma_j = gamma rho / (P_i 1)_j (recomputed inside
+ * the projector), T = min_i T_i with T_i = rho p_i / (gamma P_i^T 1) for data blocks and the
+ * scalar form for prior blocks; T = 0 where no block sees a voxel.  x = max(x0, 0) (the first
+ * primal step of Algorithm 2 with zbar = 0), y = 0, z = 0, prior duals 0.  x0 = NULL: zeros. */
+int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int where,
+                void* stream);
+
+/* Runs n SPDHG iterations (Algorithm 2) on the block indices blocks[0..n-1] (host array).
+ * Each iteration updates the selected dual block, z, and then takes the next primal step, so
+ * after the call the context's x is the primal iterate that opens the following iteration. */
+int spdhg_iterate(spdhg_ctx* ctx, const int32_t* blocks, int n, void* stream);
+
+enum { SPDHG_STATE_X = 0, SPDHG_STATE_Z = 1, SPDHG_STATE_T = 2, SPDHG_STATE_Y = 3,
+       SPDHG_STATE_Q = 4, SPDHG_STATE_SIGMA = 5, SPDHG_STATE_W = 6, SPDHG_STATE_ZW = 7,
+       SPDHG_STATE_Q2 = 8 };
+/* Copies a state array into dst (host or device per `where`): X, Z, T (N floats), Y, SIGMA
+ * (M floats; SIGMA is computed on request), Q (3N: first prior dual, components x,y,z), and for
+ * TGV W (3N), ZW (3N), Q2 (6N: xx,yy,zz,xy,xz,yz). */
+int spdhg_get(spdhg_ctx* ctx, int what, void* dst, int where, void* stream);
+
+/* Psi(x) in FP64 (Problem "PET Reconstruction with Subsets"): out[0] = sum_j varphi_j((P x)_j)
+ * (Eq. EQU:LOCALDISTANCE), out[1] = alpha R(x) for the prior of the last spdhg_setup (0 if none),
+ * out[2] = out[0] + out[1].  x = NULL uses the context's current iterate (and w for TGV). */
+int spdhg_objective(spdhg_ctx* ctx, const float* x, int where, double out[3], void* stream);
+
+/* Sampling probabilities p_i of the blocks for the current parameters (Sec. 4.2). */
+int spdhg_probabilities(const spdhg_ctx* ctx, double* probs, int* n_blocks);
+
+/* Block indices drawn with probabilities probs[0..n_blocks-1]: draw k uses the SplitMix64
+ * output number offset+k of the stream seeded with `seed`, its top 53 bits as a uniform u in
+ * [0,1), and the first block whose cumulative probability exceeds u (Remark "Sampling"). */
+int spdhg_sample(uint64_t seed, uint64_t offset, int n, const double* probs, int n_blocks,
+                 int32_t* out);
+
+/* Full reconstruction: spdhg_setup(params, x_inout) then params->epochs epochs of
+ * iterations_per_epoch draws each (2m for balanced sampling), evaluating Psi every
+ * objective_every epochs; the final iterate is written back to x_inout (host or device). */
+int spdhg_run(spdhg_ctx* ctx, const spdhg_params* params, float* x_inout, int where,
+              spdhg_report* report, void* stream);
+
+/* Kernel classes timed by the per-launch profiler. */
+enum { SPDHG_KERNEL_FORWARD = 0,   /* subset projection fused with the KL dual prox */
+       SPDHG_KERNEL_BACKWARD = 1,  /* subset backprojection fused with z and the primal step */
+       SPDHG_KERNEL_PRIOR = 2,     /* TV / dTV / aTV dual step fused with z and the primal step */
+       SPDHG_KERNEL_TGV = 3,       /* TGV dual steps */
+       SPDHG_KERNEL_WSTEP = 4,     /* TGV primal step of w in data iterations */
+       SPDHG_KERNEL_KINDS = 5 };
+
+/* Enables (1) or disables (0) per-launch timing of the iteration kernels with CUDA events on the
+ * launching stream, and clears the accumulated figures. */
+int spdhg_profile(spdhg_ctx* ctx, int enable);
+
+/* Synchronises the recorded events and returns, per kernel class k < n (n <= SPDHG_KERNEL_KINDS),
+ * the summed device time ms[k] and the launch count launches[k] since the last spdhg_profile. */
+int spdhg_profile_read(spdhg_ctx* ctx, double* ms, int64_t* launches, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPDHG_H */

@@ -1,0 +1,157 @@
+"""ctypes binding of include/spdhg.h (argument marshalling only).
+
+Every function here forwards to the CUDA library libspdhg.so; nothing is computed in Python.
+If the library has not been built (``__graft_entry__.build()`` or
+``python -m paper_1808_07150_gb300._build_ext``) loading fails loudly: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build_ext
+
+OK = 0
+ERR_ARG, ERR_CUDA, ERR_OOM, ERR_DATA, ERR_TIMEOUT, ERR_DIVERGED, ERR_STATE, ERR_UNSUPPORTED = range(-1, -9, -1)
+WHERE_HOST, WHERE_DEVICE = 0, 1
+PRIOR = {"none": 0, "tv": 1, "dtv": 2, "atv": 3, "tgv": 4}
+SAMPLING = {"balanced": 0, "uniform": 1}
+STATE = {"x": 0, "z": 1, "T": 2, "y": 3, "q": 4, "sigma": 5, "w": 6, "zw": 7, "q2": 8}
+
+_EXPORTS = [
+    "spdhg_create", "spdhg_destroy", "spdhg_last_error", "spdhg_sizes", "spdhg_set_data",
+    "spdhg_project", "spdhg_backproject", "spdhg_setup", "spdhg_iterate", "spdhg_get",
+    "spdhg_objective", "spdhg_probabilities", "spdhg_sample", "spdhg_run", "spdhg_profile",
+    "spdhg_profile_read",
+]
+KERNELS = ["forward", "backward", "prior", "tgv", "w_step"]
+
+
+class SpdhgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"spdhg error {code}: {msg}")
+        self.code = code
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("vx", ctypes.c_double), ("vy", ctypes.c_double), ("vz", ctypes.c_double),
+        ("n_radial", ctypes.c_int), ("d_radial", ctypes.c_double), ("n_views", ctypes.c_int),
+        ("radius", ctypes.c_double), ("n_segments", ctypes.c_int),
+        ("seg_n", ctypes.POINTER(ctypes.c_int)), ("seg_zmid0", ctypes.POINTER(ctypes.c_double)),
+        ("seg_dzmid", ctypes.POINTER(ctypes.c_double)), ("seg_dz", ctypes.POINTER(ctypes.c_double)),
+        ("n_subsets", ctypes.c_int),
+    ]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("prior", ctypes.c_int), ("alpha", ctypes.c_double), ("alpha0", ctypes.c_double),
+        ("alpha1", ctypes.c_double), ("dtv_gamma", ctypes.c_double), ("dtv_eta_frac", ctypes.c_double),
+        ("sampling", ctypes.c_int), ("precond", ctypes.c_int), ("rho", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64), ("epochs", ctypes.c_int),
+        ("objective_every", ctypes.c_int),
+    ]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [
+        ("epochs_done", ctypes.c_int), ("iterations_done", ctypes.c_int64),
+        ("objective", ctypes.POINTER(ctypes.c_double)), ("epoch_ms", ctypes.POINTER(ctypes.c_double)),
+    ]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build_ext.LIB
+
+
+def lib():
+    """The loaded libspdhg.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        path = _build_ext.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libspdhg.so not built ({path}); run __graft_entry__.build() first")
+        L = ctypes.CDLL(path)
+        vp, i32, i64, u64, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+        P = ctypes.POINTER
+        sig = {
+            "spdhg_create": ([P(Geometry), P(vp)], i32),
+            "spdhg_destroy": ([vp], None),
+            "spdhg_last_error": ([vp], ctypes.c_char_p),
+            "spdhg_sizes": ([vp, P(i64), P(i64), P(i32)], i32),
+            "spdhg_set_data": ([vp, vp, vp, vp, vp, i32], i32),
+            "spdhg_project": ([vp, vp, vp, i32, vp], i32),
+            "spdhg_backproject": ([vp, vp, vp, i32, vp], i32),
+            "spdhg_setup": ([vp, P(Params), vp, i32, vp], i32),
+            "spdhg_iterate": ([vp, P(ctypes.c_int32), i32, vp], i32),
+            "spdhg_get": ([vp, i32, vp, i32, vp], i32),
+            "spdhg_objective": ([vp, vp, i32, P(dp), vp], i32),
+            "spdhg_probabilities": ([vp, P(dp), P(i32)], i32),
+            "spdhg_sample": ([u64, u64, i32, P(dp), i32, P(ctypes.c_int32)], i32),
+            "spdhg_run": ([vp, P(Params), vp, i32, P(Report), vp], i32),
+            "spdhg_profile": ([vp, i32], i32),
+            "spdhg_profile_read": ([vp, P(dp), P(i64), i32], i32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_EXPORTS)
+
+
+def check(code, ctx=None):
+    if code != OK:
+        msg = lib().spdhg_last_error(ctx).decode() if ctx else ""
+        raise SpdhgError(code, msg)
+
+
+def make_geometry(sc):
+    """ctypes Geometry from any object with the Scanner fields; returns (struct, keepalive)."""
+    n = len(sc.seg_n)
+    keep = [(ctypes.c_int * n)(*sc.seg_n), (ctypes.c_double * n)(*sc.seg_zmid0),
+            (ctypes.c_double * n)(*sc.seg_dzmid), (ctypes.c_double * n)(*sc.seg_dz)]
+    g = Geometry(sc.nx, sc.ny, sc.nz, sc.vx, sc.vy, sc.vz, sc.n_radial, sc.d_radial, sc.n_views,
+                 sc.radius, n, keep[0], keep[1], keep[2], keep[3], sc.n_subsets)
+    return g, keep
+
+
+def make_params(prior="tv", alpha=0.1, alpha0=0.2, alpha1=0.1, dtv_gamma=0.995, dtv_eta_frac=0.01,
+                sampling="balanced", precond=True, rho=0.99, gamma=1.0, seed=1808, epochs=1,
+                objective_every=0):
+    return Params(PRIOR[prior], alpha, alpha0, alpha1, dtv_gamma, dtv_eta_frac, SAMPLING[sampling],
+                  int(bool(precond)), rho, gamma, seed, epochs, objective_every)
+
+
+def pointer(a, numel=None, dtype=np.float32):
+    """(address, where) of a torch tensor or numpy array; None -> (None, WHERE_HOST)."""
+    if a is None:
+        return None, WHERE_HOST
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != {np.float32: torch.float32, np.int32: torch.int32}[dtype]:
+                raise TypeError(f"expected {dtype.__name__} tensor, got {a.dtype}")
+            if not a.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            if numel is not None and a.numel() != numel:
+                raise ValueError(f"expected {numel} elements, got {a.numel()}")
+            return a.data_ptr(), (WHERE_DEVICE if a.is_cuda else WHERE_HOST)
+    except ImportError:  # pragma: no cover
+        pass
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a C-contiguous {np.dtype(dtype).name} numpy array or tensor")
+    if numel is not None and a.size != numel:
+        raise ValueError(f"expected {numel} elements, got {a.size}")
+    return a.ctypes.data, WHERE_HOST

@@ -1,0 +1,781 @@
+// C ABI of libspdhg: context management, data upload, projector entry points, step-size
+// setup, the SPDHG iteration driver, the sampler and the FP64 objective.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace spdhg;
+
+namespace {
+
+int fail(spdhg_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? SPDHG_ERR_OOM : SPDHG_ERR_CUDA,     \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+  } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n) {
+  if (*p) return cudaSuccess;
+  return cudaMalloc((void**)p, n * sizeof(T) + 16);
+}
+
+__global__ void k_fill(float* p, int64_t n, float v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+__global__ void k_clamp_copy(float* dst, const float* src, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = fmaxf(src[i], 0.f);
+}
+
+// T = min(T, t_prior); voxels that no block sees (+inf) get T = 0.
+__global__ void k_finalize_T(float* T, int64_t n, float t_prior) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float t = fminf(T[i], t_prior);
+    T[i] = isinf(t) ? 0.f : t;
+  }
+}
+
+// counts values that are non-finite or violate the bound (mode 0: >= 0, mode 1: > 0)
+__global__ void k_validate(const float* p, int64_t n, int mode, unsigned long long* bad) {
+  unsigned long long cnt = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = p[i];
+    const bool ok = isfinite(v) && (mode == 0 ? v >= 0.f : v > 0.f);
+    cnt += ok ? 0ull : 1ull;
+  }
+  if (cnt) atomicAdd(bad, cnt);
+}
+
+int grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
+}
+
+uint64_t splitmix64(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+double grad_norm(int nx, int ny, int nz) {
+  // largest eigenvalue of the Neumann Laplacian of n points: 4 sin^2(pi (n-1) / (2n))
+  const double pi = 3.14159265358979323846;
+  double s = 0.0;
+  for (int n : {nx, ny, nz}) s += 4.0 * pow(sin(pi * (n - 1) / (2.0 * n)), 2);
+  return sqrt(s);
+}
+
+int n_prior_blocks(int prior) {
+  switch (prior) {
+    case SPDHG_PRIOR_NONE: return 0;
+    case SPDHG_PRIOR_TGV: return 2;
+    default: return 1;
+  }
+}
+
+std::vector<double> block_probs(int m, int prior, int sampling) {
+  const int nb = n_prior_blocks(prior);
+  const int n = m + nb;
+  std::vector<double> p(n);
+  if (nb == 0 || sampling == SPDHG_SAMPLING_UNIFORM) {
+    for (auto& v : p) v = 1.0 / n;
+  } else {
+    for (int i = 0; i < m; ++i) p[i] = 1.0 / (2.0 * m);
+    for (int i = m; i < n; ++i) p[i] = 0.5 / nb;
+  }
+  return p;
+}
+
+int check_device(spdhg_ctx* ctx) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(ctx, SPDHG_ERR_CUDA, "cudaGetDevice failed");
+  if (dev != ctx->device) return fail(ctx, SPDHG_ERR_STATE, "current CUDA device differs from the context's device");
+  return SPDHG_OK;
+}
+
+cudaEvent_t prof_event(spdhg_ctx* ctx) {
+  if (!ctx->prof_pool.empty()) {
+    cudaEvent_t e = ctx->prof_pool.back();
+    ctx->prof_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Records an event pair around one kernel launch when profiling is on.
+struct ProfScope {
+  spdhg_ctx* ctx;
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  ProfScope(spdhg_ctx* c, int k, cudaStream_t st) : ctx(c), kind(k), s(st) {
+    if (ctx->profiling) {
+      a = prof_event(ctx);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~ProfScope() {
+    if (a) {
+      cudaEvent_t b = prof_event(ctx);
+      cudaEventRecord(b, s);
+      ctx->prof_pending.push_back({kind, a, b});
+    }
+  }
+};
+
+int copy_in(spdhg_ctx* ctx, float* dst, const float* src, int64_t n, int where, cudaStream_t s) {
+  CK(cudaMemcpyAsync(dst, src, n * sizeof(float), where == SPDHG_WHERE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+  return SPDHG_OK;
+}
+
+int copy_out(spdhg_ctx* ctx, void* dst, const float* src, int64_t n, int where, cudaStream_t s) {
+  CK(cudaMemcpyAsync(dst, src, n * sizeof(float), where == SPDHG_WHERE_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+  if (where == SPDHG_WHERE_HOST) CK(cudaStreamSynchronize(s));
+  return SPDHG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
+  if (!out) return SPDHG_ERR_ARG;
+  *out = nullptr;
+  if (!geom || !geom->seg_n || !geom->seg_zmid0 || !geom->seg_dzmid || !geom->seg_dz) return SPDHG_ERR_ARG;
+  const spdhg_geometry& g = *geom;
+  if (g.nx < 1 || g.ny < 1 || g.nz < 1 || g.n_radial < 1 || g.n_views < 1 || g.n_segments < 1 ||
+      g.n_subsets < 1 || g.n_subsets > g.n_views || !(g.vx > 0) || !(g.vy > 0) || !(g.vz > 0) ||
+      !(g.d_radial > 0) || !(g.radius > 0))
+    return SPDHG_ERR_ARG;
+  if (fabs(g.vx - g.vy) > 1e-9 * g.vx) return SPDHG_ERR_UNSUPPORTED;
+  if (g.n_segments > kMaxSeg || g.nz > 256) return SPDHG_ERR_UNSUPPORTED;
+  const double smax = 0.5 * (g.n_radial - 1) * g.d_radial;
+  if (!(g.radius > smax)) return SPDHG_ERR_UNSUPPORTED;
+  int P = 0;
+  double kappa_max = 0.0;
+  const double hmin = sqrt(g.radius * g.radius - smax * smax);
+  for (int k = 0; k < g.n_segments; ++k) {
+    if (g.seg_n[k] < 1) return SPDHG_ERR_ARG;
+    if (g.seg_n[k] > 1 && fabs(g.seg_dzmid[k] - g.vz) > 1e-9 * g.vz) return SPDHG_ERR_UNSUPPORTED;
+    P += g.seg_n[k];
+    kappa_max = std::max(kappa_max, fabs(g.seg_dz[k]) / (2.0 * hmin * g.vz));
+  }
+  if (P > 512 * kMaxPlanesPerThread) return SPDHG_ERR_UNSUPPORTED;
+  const double dt_max = sqrt(2.0) * g.vx;  // longest transaxial chord of a pixel
+  const int taps = kappa_max == 0.0 ? 1 : (int)ceil(1.0 + kappa_max * dt_max * (1.0 + 1e-6));
+  if (taps > kMaxTaps) return SPDHG_ERR_UNSUPPORTED;
+  const int nr_max = (int)floor(sqrt(2.0) * g.vx / g.d_radial) + 4;
+  if (nr_max > 16) return SPDHG_ERR_UNSUPPORTED;
+
+  spdhg_ctx* ctx = new spdhg_ctx();
+  ctx->geom = g;
+  ctx->seg_n.assign(g.seg_n, g.seg_n + g.n_segments);
+  ctx->seg_zmid0.assign(g.seg_zmid0, g.seg_zmid0 + g.n_segments);
+  ctx->seg_dzmid.assign(g.seg_dzmid, g.seg_dzmid + g.n_segments);
+  ctx->seg_dz.assign(g.seg_dz, g.seg_dz + g.n_segments);
+  ctx->geom.seg_n = ctx->seg_n.data();
+  ctx->geom.seg_zmid0 = ctx->seg_zmid0.data();
+  ctx->geom.seg_dzmid = ctx->seg_dzmid.data();
+  ctx->geom.seg_dz = ctx->seg_dz.data();
+  cudaGetDevice(&ctx->device);
+  ctx->N = (int64_t)g.nx * g.ny * g.nz;
+  ctx->M = (int64_t)g.n_views * g.n_radial * P;
+  ctx->max_subset_bins = (int64_t)((g.n_views + g.n_subsets - 1) / g.n_subsets) * g.n_radial * P;
+
+  // device tables
+  const double pi = 3.14159265358979323846;
+  std::vector<float2> cs(g.n_views);
+  for (int v = 0; v < g.n_views; ++v) {
+    double c = cos(pi * v / g.n_views), s = sin(pi * v / g.n_views);
+    if (fabs(c) < 1e-12) c = 0.0;
+    if (fabs(s) < 1e-12) s = 0.0;
+    cs[v] = make_float2((float)c, (float)s);
+  }
+  const double loz = -0.5 * g.nz * g.vz;
+  std::vector<SegDev> seg(g.n_segments);
+  std::vector<int> plane_seg(P);
+  int p0 = 0;
+  for (int k = 0; k < g.n_segments; ++k) {
+    seg[k].p0 = p0;
+    seg[k].n = g.seg_n[k];
+    seg[k].f = (float)((g.seg_zmid0[k] - loz) / g.vz);
+    seg[k].dz = (float)g.seg_dz[k];
+    for (int q = 0; q < g.seg_n[k]; ++q) plane_seg[p0 + q] = k;
+    p0 += g.seg_n[k];
+  }
+  auto cleanup_fail = [&](cudaError_t e) {
+    std::string msg = std::string("device table upload failed: ") + cudaGetErrorString(e);
+    spdhg_destroy(ctx);
+    (void)msg;
+    return e == cudaErrorMemoryAllocation ? SPDHG_ERR_OOM : SPDHG_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaMalloc(&ctx->d_view_cs, sizeof(float2) * g.n_views)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMalloc(&ctx->d_seg, sizeof(SegDev) * g.n_segments)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMalloc(&ctx->d_plane_seg, sizeof(int) * P)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMemcpy(ctx->d_view_cs, cs.data(), sizeof(float2) * g.n_views, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMemcpy(ctx->d_seg, seg.data(), sizeof(SegDev) * g.n_segments, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMemcpy(ctx->d_plane_seg, plane_seg.data(), sizeof(int) * P, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
+
+  DevGeom& d = ctx->dg;
+  d.nx = g.nx;
+  d.ny = g.ny;
+  d.nz = g.nz;
+  d.vx = (float)g.vx;
+  d.vz = (float)g.vz;
+  d.lox = (float)(-0.5 * g.nx * g.vx);
+  d.loy = (float)(-0.5 * g.ny * g.vy);
+  d.inv_vx = (float)(1.0 / g.vx);
+  d.R = g.n_radial;
+  d.V = g.n_views;
+  d.P = P;
+  d.m = g.n_subsets;
+  d.n_seg = g.n_segments;
+  d.taps = taps;
+  d.nr_max = nr_max;
+  d.d_radial = (float)g.d_radial;
+  d.half_R = (float)(0.5 * (g.n_radial - 1));
+  d.radius2 = (float)(g.radius * g.radius);
+  d.view_cs = ctx->d_view_cs;
+  d.seg = ctx->d_seg;
+  d.plane_seg = ctx->d_plane_seg;
+  *out = ctx;
+  return SPDHG_OK;
+}
+
+void spdhg_destroy(spdhg_ctx* ctx) {
+  if (!ctx) return;
+  void* ptrs[] = {ctx->d_view_cs, ctx->d_seg, ctx->d_plane_seg, ctx->b, ctx->r, ctx->mult, ctx->side,
+                  ctx->x[0], ctx->x[1], ctx->z, ctx->T, ctx->y, ctx->wdy, ctx->q[0], ctx->q[1],
+                  ctx->w[0], ctx->w[1], ctx->zw, ctx->q2[0], ctx->q2[1], ctx->tmp_sino, ctx->tmp_img,
+                  ctx->red, ctx->red_out};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (auto& r : ctx->prof_pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char* spdhg_last_error(const spdhg_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int spdhg_sizes(const spdhg_ctx* ctx, int64_t* n_voxels, int64_t* n_bins, int* n_blocks) {
+  if (!ctx) return SPDHG_ERR_ARG;
+  if (n_voxels) *n_voxels = ctx->N;
+  if (n_bins) *n_bins = ctx->M;
+  if (n_blocks) *n_blocks = ctx->is_setup ? (int)ctx->probs.size() : ctx->geom.n_subsets;
+  return SPDHG_OK;
+}
+
+int spdhg_set_data(spdhg_ctx* ctx, const float* b, const float* r, const float* mult, const float* side,
+                   int where) {
+  if (!ctx) return SPDHG_ERR_ARG;
+  if (!b || !r || (where != SPDHG_WHERE_HOST && where != SPDHG_WHERE_DEVICE)) return fail(ctx, SPDHG_ERR_ARG, "b and r are required");
+  if (int st = check_device(ctx)) return st;
+  CK(dalloc(&ctx->b, ctx->M));
+  CK(dalloc(&ctx->r, ctx->M));
+  CK(dalloc(&ctx->red, 2048));
+  CK(dalloc(&ctx->red_out, 8));
+  cudaStream_t s = 0;
+  if (int st = copy_in(ctx, ctx->b, b, ctx->M, where, s)) return st;
+  if (int st = copy_in(ctx, ctx->r, r, ctx->M, where, s)) return st;
+  ctx->has_mult = mult != nullptr;
+  if (mult) {
+    CK(dalloc(&ctx->mult, ctx->M));
+    if (int st = copy_in(ctx, ctx->mult, mult, ctx->M, where, s)) return st;
+  }
+  ctx->has_side = side != nullptr;
+  if (side) {
+    CK(dalloc(&ctx->side, ctx->N));
+    if (int st = copy_in(ctx, ctx->side, side, ctx->N, where, s)) return st;
+  }
+  unsigned long long* bad = reinterpret_cast<unsigned long long*>(ctx->red_out);
+  CK(cudaMemsetAsync(bad, 0, 8 * sizeof(double), s));
+  k_validate<<<grid_for(ctx->M), 256, 0, s>>>(ctx->b, ctx->M, 0, bad);
+  k_validate<<<grid_for(ctx->M), 256, 0, s>>>(ctx->r, ctx->M, 0, bad + 1);
+  if (mult) k_validate<<<grid_for(ctx->M), 256, 0, s>>>(ctx->mult, ctx->M, 1, bad + 2);
+  if (side) k_validate<<<grid_for(ctx->N), 256, 0, s>>>(ctx->side, ctx->N, 0, bad + 3);
+  CK(cudaGetLastError());
+  unsigned long long h[4];
+  CK(cudaMemcpy(h, bad, sizeof(h), cudaMemcpyDeviceToHost));
+  if (h[0] || h[1] || h[2] || h[3]) {
+    ctx->has_data = false;
+    char msg[256];
+    snprintf(msg, sizeof msg, "invalid data: %llu bad b, %llu bad r, %llu bad mult (<=0), %llu bad side", h[0], h[1], h[2], h[3]);
+    return fail(ctx, SPDHG_ERR_DATA, msg);
+  }
+  ctx->has_data = true;
+  ctx->is_setup = false;
+  return SPDHG_OK;
+}
+
+int spdhg_project(spdhg_ctx* ctx, const float* x, float* y, int subset, void* stream) {
+  if (!ctx || !x || !y) return SPDHG_ERR_ARG;
+  if (subset < -1 || subset >= ctx->geom.n_subsets) return fail(ctx, SPDHG_ERR_ARG, "subset out of range");
+  if (int st = check_device(ctx)) return st;
+  FwdArgs a{};
+  a.x = x;
+  a.out = y;
+  a.mult = ctx->has_mult ? ctx->mult : nullptr;
+  CK(launch_forward(ctx->dg, subset, FWD_PROJECT, a, (cudaStream_t)stream));
+  return SPDHG_OK;
+}
+
+int spdhg_backproject(spdhg_ctx* ctx, const float* y, float* x, int subset, void* stream) {
+  if (!ctx || !x || !y) return SPDHG_ERR_ARG;
+  if (subset < -1 || subset >= ctx->geom.n_subsets) return fail(ctx, SPDHG_ERR_ARG, "subset out of range");
+  if (int st = check_device(ctx)) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  // subset -1 uses a full-size scratch sinogram
+  float* w = nullptr;
+  if (subset < 0) {
+    CK(dalloc(&ctx->tmp_sino, ctx->M));
+    w = ctx->tmp_sino;
+  } else {
+    CK(dalloc(&ctx->wdy, ctx->max_subset_bins));
+    w = ctx->wdy;
+  }
+  CK(launch_gather_subset(ctx->dg, subset, y, ctx->has_mult ? ctx->mult : nullptr, w, s));
+  BwdArgs a{};
+  a.w = w;
+  a.out = x;
+  CK(launch_backward(ctx->dg, subset, BWD_OUT, a, s));
+  return SPDHG_OK;
+}
+
+int spdhg_probabilities(const spdhg_ctx* ctx, double* probs, int* n_blocks) {
+  if (!ctx || !n_blocks) return SPDHG_ERR_ARG;
+  if (!ctx->is_setup) return SPDHG_ERR_STATE;
+  *n_blocks = (int)ctx->probs.size();
+  if (probs)
+    for (size_t i = 0; i < ctx->probs.size(); ++i) probs[i] = ctx->probs[i];
+  return SPDHG_OK;
+}
+
+int spdhg_sample(uint64_t seed, uint64_t offset, int n, const double* probs, int n_blocks, int32_t* out) {
+  if (n < 0 || n_blocks < 1 || !probs || (n > 0 && !out)) return SPDHG_ERR_ARG;
+  std::vector<double> cum(n_blocks);
+  double acc = 0.0;
+  for (int i = 0; i < n_blocks; ++i) {
+    if (!(probs[i] >= 0.0)) return SPDHG_ERR_ARG;
+    acc += probs[i];
+    cum[i] = acc;
+  }
+  for (int k = 0; k < n; ++k) {
+    const double u = (double)(splitmix64(seed, offset + (uint64_t)k) >> 11) * (1.0 / 9007199254740992.0);
+    int i = 0;
+    while (i < n_blocks - 1 && !(u < cum[i])) ++i;
+    out[k] = i;
+  }
+  return SPDHG_OK;
+}
+
+int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int where, void* stream) {
+  if (!ctx || !params) return SPDHG_ERR_ARG;
+  if (int st = check_device(ctx)) return st;
+  if (!ctx->has_data) return fail(ctx, SPDHG_ERR_STATE, "spdhg_set_data must be called before spdhg_setup");
+  spdhg_params p = *params;
+  if (!(p.rho > 0)) p.rho = 0.99;
+  if (!(p.gamma > 0)) p.gamma = 1.0;
+  if (p.prior < SPDHG_PRIOR_NONE || p.prior > SPDHG_PRIOR_TGV) return fail(ctx, SPDHG_ERR_ARG, "unknown prior");
+  if (!(p.rho < 1.0)) return fail(ctx, SPDHG_ERR_ARG, "rho must be < 1");
+  if (p.prior == SPDHG_PRIOR_DTV && !ctx->has_side) return fail(ctx, SPDHG_ERR_STATE, "dTV needs a side image (spdhg_set_data)");
+  if (p.prior == SPDHG_PRIOR_DTV && !(p.dtv_gamma >= 0.0 && p.dtv_gamma < 1.0)) return fail(ctx, SPDHG_ERR_ARG, "dtv_gamma must be in [0, 1)");
+  if (p.prior == SPDHG_PRIOR_TGV ? !(p.alpha0 > 0 && p.alpha1 > 0) : (p.prior != SPDHG_PRIOR_NONE && !(p.alpha > 0)))
+    return fail(ctx, SPDHG_ERR_ARG, "prior weights must be positive");
+  if (!p.precond) return fail(ctx, SPDHG_ERR_UNSUPPORTED, "scalar data step sizes are not available; use precond = 1");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = ctx->N, M = ctx->M;
+  const int m = ctx->geom.n_subsets;
+
+  CK(dalloc(&ctx->x[0], N));
+  CK(dalloc(&ctx->x[1], N));
+  CK(dalloc(&ctx->z, N));
+  CK(dalloc(&ctx->T, N));
+  CK(dalloc(&ctx->y, M));
+  CK(dalloc(&ctx->wdy, ctx->max_subset_bins));
+  const bool tgv = p.prior == SPDHG_PRIOR_TGV;
+  if (p.prior != SPDHG_PRIOR_NONE) {
+    CK(dalloc(&ctx->q[0], 3 * N));
+    CK(dalloc(&ctx->q[1], 3 * N));
+  }
+  if (tgv) {
+    CK(dalloc(&ctx->w[0], 3 * N));
+    CK(dalloc(&ctx->w[1], 3 * N));
+    CK(dalloc(&ctx->zw, 3 * N));
+    CK(dalloc(&ctx->q2[0], 6 * N));
+    CK(dalloc(&ctx->q2[1], 6 * N));
+  }
+
+  ctx->params = p;
+  ctx->probs = block_probs(m, p.prior, p.sampling);
+  const double gn = grad_norm(ctx->geom.nx, ctx->geom.ny, ctx->geom.nz);
+
+  // T = min over data blocks of rho p_i / (gamma P_i^T 1)  (Eq. EQU:STEPSIZE:PRECOND)
+  k_fill<<<grid_for(N), 256, 0, s>>>(ctx->T, N, INFINITY);
+  CK(cudaGetLastError());
+  for (int i = 0; i < m; ++i) {
+    if (ctx->has_mult) {
+      CK(launch_gather_subset(ctx->dg, i, ctx->mult, nullptr, ctx->wdy, s));
+    } else {
+      k_fill<<<grid_for(ctx->max_subset_bins), 256, 0, s>>>(ctx->wdy, ctx->max_subset_bins, 1.f);
+      CK(cudaGetLastError());
+    }
+    BwdArgs a{};
+    a.w = ctx->wdy;
+    a.T = ctx->T;
+    a.sens_num = (float)(p.rho * ctx->probs[i] / p.gamma);
+    CK(launch_backward(ctx->dg, i, BWD_SENS, a, s));
+  }
+  // prior blocks: scalar steps (Eq. EQU:STEPSIZE:SCALAR)
+  ctx->sigma_prior.clear();
+  float t_prior = INFINITY;
+  if (tgv) {
+    const double n0 = sqrt(gn * gn + 1.0), n1 = gn;  // ||(grad, -I)||, bound on ||E||
+    const double T0 = p.rho * ctx->probs[m] / (p.gamma * n0), T1 = p.rho * ctx->probs[m + 1] / (p.gamma * n1);
+    ctx->sigma_prior = {(float)(p.gamma * p.rho / n0), (float)(p.gamma * p.rho / n1)};
+    t_prior = (float)T0;
+    ctx->Tw = (float)std::min(T0, T1);
+  } else if (p.prior != SPDHG_PRIOR_NONE) {
+    ctx->sigma_prior = {(float)(p.gamma * p.rho / gn)};
+    t_prior = (float)(p.rho * ctx->probs[m] / (p.gamma * gn));
+  }
+  k_finalize_T<<<grid_for(N), 256, 0, s>>>(ctx->T, N, t_prior);
+  CK(cudaGetLastError());
+
+  if (p.prior == SPDHG_PRIOR_DTV) {
+    CK(launch_side_max_grad(ctx->dg, ctx->side, ctx->red, ctx->red_blocks, ctx->red_out, s));
+    double gmax = 0.0;
+    CK(cudaMemcpyAsync(&gmax, ctx->red_out, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double eta = gmax > 0 ? p.dtv_eta_frac * gmax : 1.0;
+    ctx->eta2 = eta * eta;
+  }
+
+  // initial state: x = max(x0, 0), y = z = q = 0
+  ctx->xcur = 0;
+  ctx->qcur = 0;
+  ctx->wcur = 0;
+  ctx->q2cur = 0;
+  if (x0) {
+    if (where == SPDHG_WHERE_HOST) {
+      CK(cudaMemcpyAsync(ctx->x[1], x0, N * sizeof(float), cudaMemcpyHostToDevice, s));
+      k_clamp_copy<<<grid_for(N), 256, 0, s>>>(ctx->x[0], ctx->x[1], N);
+    } else {
+      k_clamp_copy<<<grid_for(N), 256, 0, s>>>(ctx->x[0], x0, N);
+    }
+    CK(cudaGetLastError());
+  } else {
+    CK(cudaMemsetAsync(ctx->x[0], 0, N * sizeof(float), s));
+  }
+  CK(cudaMemsetAsync(ctx->z, 0, N * sizeof(float), s));
+  CK(cudaMemsetAsync(ctx->y, 0, M * sizeof(float), s));
+  if (p.prior != SPDHG_PRIOR_NONE) CK(cudaMemsetAsync(ctx->q[0], 0, 3 * N * sizeof(float), s));
+  if (tgv) {
+    CK(cudaMemsetAsync(ctx->w[0], 0, 3 * N * sizeof(float), s));
+    CK(cudaMemsetAsync(ctx->zw, 0, 3 * N * sizeof(float), s));
+    CK(cudaMemsetAsync(ctx->q2[0], 0, 6 * N * sizeof(float), s));
+  }
+  ctx->iterations = 0;
+  ctx->is_setup = true;
+  return SPDHG_OK;
+}
+
+int spdhg_iterate(spdhg_ctx* ctx, const int32_t* blocks, int n, void* stream) {
+  if (!ctx || (n > 0 && !blocks) || n < 0) return SPDHG_ERR_ARG;
+  if (!ctx->is_setup) return fail(ctx, SPDHG_ERR_STATE, "spdhg_setup must be called before spdhg_iterate");
+  if (int st = check_device(ctx)) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int m = ctx->geom.n_subsets;
+  const int nblk = (int)ctx->probs.size();
+  const spdhg_params& p = ctx->params;
+  for (int k = 0; k < n; ++k) {
+    const int i = blocks[k];
+    if (i < 0 || i >= nblk) return fail(ctx, SPDHG_ERR_ARG, "block index out of range");
+    const float inv_p = (float)(1.0 / ctx->probs[i]);
+    if (i < m) {
+      FwdArgs fa{};
+      fa.x = ctx->x[ctx->xcur];
+      fa.mult = ctx->has_mult ? ctx->mult : nullptr;
+      fa.b = ctx->b;
+      fa.r = ctx->r;
+      fa.y = ctx->y;
+      fa.wdy = ctx->wdy;
+      fa.gamma_rho = (float)(p.gamma * p.rho);
+      {
+        ProfScope ps(ctx, SPDHG_KERNEL_FORWARD, s);
+        CK(launch_forward(ctx->dg, i, FWD_DATA, fa, s));
+      }
+      BwdArgs ba{};
+      ba.w = ctx->wdy;
+      ba.x = ctx->x[ctx->xcur];
+      ba.z = ctx->z;
+      ba.T = ctx->T;
+      ba.inv_p = inv_p;
+      {
+        ProfScope ps(ctx, SPDHG_KERNEL_BACKWARD, s);
+        CK(launch_backward(ctx->dg, i, BWD_UPDATE, ba, s));
+      }
+      if (p.prior == SPDHG_PRIOR_TGV) {
+        ProfScope ps(ctx, SPDHG_KERNEL_WSTEP, s);
+        CK(launch_w_step(ctx->dg, ctx->w[ctx->wcur], ctx->zw, ctx->Tw, s));
+      }
+    } else if (p.prior == SPDHG_PRIOR_TGV) {
+      const int kblk = i - m;
+      TgvArgs ta{};
+      ta.block = kblk;
+      ta.u_in = ctx->x[ctx->xcur];
+      ta.u_out = ctx->x[1 - ctx->xcur];
+      ta.w_in = ctx->w[ctx->wcur];
+      ta.w_out = ctx->w[1 - ctx->wcur];
+      if (kblk == 0) {
+        ta.q_in = ctx->q[ctx->qcur];
+        ta.q_out = ctx->q[1 - ctx->qcur];
+        ta.alpha = (float)p.alpha0;
+      } else {
+        ta.q_in = ctx->q2[ctx->q2cur];
+        ta.q_out = ctx->q2[1 - ctx->q2cur];
+        ta.alpha = (float)p.alpha1;
+      }
+      ta.zu = ctx->z;
+      ta.zw = ctx->zw;
+      ta.Tu = ctx->T;
+      ta.Tw = ctx->Tw;
+      ta.sigma = ctx->sigma_prior[kblk];
+      ta.inv_p = inv_p;
+      {
+        ProfScope ps(ctx, SPDHG_KERNEL_TGV, s);
+        CK(launch_tgv(ctx->dg, ta, s));
+      }
+      ctx->xcur ^= 1;
+      ctx->wcur ^= 1;
+      if (kblk == 0) ctx->qcur ^= 1;
+      else ctx->q2cur ^= 1;
+    } else {
+      PriorArgs pa{};
+      pa.kind = p.prior;
+      pa.x_in = ctx->x[ctx->xcur];
+      pa.x_out = ctx->x[1 - ctx->xcur];
+      pa.q_in = ctx->q[ctx->qcur];
+      pa.q_out = ctx->q[1 - ctx->qcur];
+      pa.z = ctx->z;
+      pa.T = ctx->T;
+      pa.side = ctx->side;
+      pa.sigma = ctx->sigma_prior[0];
+      pa.alpha = (float)p.alpha;
+      pa.inv_p = inv_p;
+      pa.gamma_d = (float)p.dtv_gamma;
+      pa.eta2 = (float)ctx->eta2;
+      {
+        ProfScope ps(ctx, SPDHG_KERNEL_PRIOR, s);
+        CK(launch_prior(ctx->dg, pa, s));
+      }
+      ctx->xcur ^= 1;
+      ctx->qcur ^= 1;
+    }
+    ++ctx->iterations;
+  }
+  return SPDHG_OK;
+}
+
+int spdhg_get(spdhg_ctx* ctx, int what, void* dst, int where, void* stream) {
+  if (!ctx || !dst) return SPDHG_ERR_ARG;
+  if (int st = check_device(ctx)) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = ctx->N, M = ctx->M;
+  if (!ctx->is_setup) return fail(ctx, SPDHG_ERR_STATE, "no state before spdhg_setup");
+  const bool tgv = ctx->params.prior == SPDHG_PRIOR_TGV;
+  switch (what) {
+    case SPDHG_STATE_X: return copy_out(ctx, dst, ctx->x[ctx->xcur], N, where, s);
+    case SPDHG_STATE_Z: return copy_out(ctx, dst, ctx->z, N, where, s);
+    case SPDHG_STATE_T: return copy_out(ctx, dst, ctx->T, N, where, s);
+    case SPDHG_STATE_Y: return copy_out(ctx, dst, ctx->y, M, where, s);
+    case SPDHG_STATE_Q:
+      if (ctx->params.prior == SPDHG_PRIOR_NONE) return fail(ctx, SPDHG_ERR_STATE, "no prior dual");
+      return copy_out(ctx, dst, ctx->q[ctx->qcur], 3 * N, where, s);
+    case SPDHG_STATE_W:
+      if (!tgv) return fail(ctx, SPDHG_ERR_STATE, "no TGV state");
+      return copy_out(ctx, dst, ctx->w[ctx->wcur], 3 * N, where, s);
+    case SPDHG_STATE_ZW:
+      if (!tgv) return fail(ctx, SPDHG_ERR_STATE, "no TGV state");
+      return copy_out(ctx, dst, ctx->zw, 3 * N, where, s);
+    case SPDHG_STATE_Q2:
+      if (!tgv) return fail(ctx, SPDHG_ERR_STATE, "no TGV state");
+      return copy_out(ctx, dst, ctx->q2[ctx->q2cur], 6 * N, where, s);
+    case SPDHG_STATE_SIGMA: {
+      float* out = nullptr;
+      if (where == SPDHG_WHERE_DEVICE) {
+        out = (float*)dst;
+      } else {
+        CK(dalloc(&ctx->tmp_sino, M));
+        out = ctx->tmp_sino;
+      }
+      FwdArgs a{};
+      a.x = ctx->x[ctx->xcur];  // unused by the sigma pass except as a valid pointer
+      a.out = out;
+      a.mult = ctx->has_mult ? ctx->mult : nullptr;
+      a.gamma_rho = (float)(ctx->params.gamma * ctx->params.rho);
+      CK(launch_forward(ctx->dg, -1, FWD_SIGMA, a, s));
+      if (where == SPDHG_WHERE_HOST) return copy_out(ctx, dst, out, M, where, s);
+      return SPDHG_OK;
+    }
+    default: return fail(ctx, SPDHG_ERR_ARG, "unknown state array");
+  }
+}
+
+int spdhg_objective(spdhg_ctx* ctx, const float* x, int where, double out[3], void* stream) {
+  if (!ctx || !out) return SPDHG_ERR_ARG;
+  if (int st = check_device(ctx)) return st;
+  if (!ctx->has_data) return fail(ctx, SPDHG_ERR_STATE, "no data");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = ctx->N, M = ctx->M;
+  CK(dalloc(&ctx->tmp_sino, M));
+  const float* xd = x;
+  if (!x) {
+    if (!ctx->is_setup) return fail(ctx, SPDHG_ERR_STATE, "no iterate before spdhg_setup");
+    xd = ctx->x[ctx->xcur];
+  } else if (where == SPDHG_WHERE_HOST) {
+    CK(dalloc(&ctx->tmp_img, N));
+    CK(cudaMemcpyAsync(ctx->tmp_img, x, N * sizeof(float), cudaMemcpyHostToDevice, s));
+    xd = ctx->tmp_img;
+  }
+  FwdArgs a{};
+  a.x = xd;
+  a.out = ctx->tmp_sino;
+  a.mult = ctx->has_mult ? ctx->mult : nullptr;
+  CK(launch_forward(ctx->dg, -1, FWD_PROJECT, a, s));
+  CK(launch_data_term(ctx->tmp_sino, ctx->b, ctx->r, M, ctx->red, ctx->red_blocks, ctx->red_out, s));
+  int kind = ctx->is_setup ? ctx->params.prior : SPDHG_PRIOR_NONE;
+  if (kind == SPDHG_PRIOR_TGV && x) kind = SPDHG_PRIOR_NONE;  // w unknown for an external u
+  if (kind != SPDHG_PRIOR_NONE) {
+    const float* w = kind == SPDHG_PRIOR_TGV ? ctx->w[ctx->wcur] : nullptr;
+    CK(launch_prior_term(ctx->dg, kind, xd, w, ctx->side, (float)ctx->params.dtv_gamma, (float)ctx->eta2,
+                         ctx->red, ctx->red_blocks, ctx->red_out + 1, s));
+  }
+  double h[3] = {0, 0, 0};
+  CK(cudaMemcpyAsync(h, ctx->red_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double prior = 0.0;
+  const spdhg_params& p = ctx->params;
+  if (kind == SPDHG_PRIOR_TGV) prior = p.alpha0 * h[1] + p.alpha1 * h[2];
+  else if (kind != SPDHG_PRIOR_NONE) prior = p.alpha * h[1];
+  out[0] = h[0];
+  out[1] = prior;
+  out[2] = h[0] + prior;
+  return SPDHG_OK;
+}
+
+int spdhg_run(spdhg_ctx* ctx, const spdhg_params* params, float* x_inout, int where, spdhg_report* rep,
+              void* stream) {
+  if (!ctx || !params || params->epochs < 0) return SPDHG_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int st = spdhg_setup(ctx, params, x_inout, where, stream)) return st;
+  const int m = ctx->geom.n_subsets;
+  double pdata = 0.0;
+  for (int i = 0; i < m; ++i) pdata += ctx->probs[i];
+  const int ipe = (int)llround(m / pdata);
+  std::vector<int32_t> seq(ipe);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  int status = SPDHG_OK;
+  const int every = params->objective_every;
+  if (rep) {
+    rep->epochs_done = 0;
+    rep->iterations_done = 0;
+    if (rep->objective)
+      for (int e = 0; e <= params->epochs; ++e) rep->objective[e] = NAN;
+  }
+  if (rep && rep->objective && every > 0) {
+    double o[3];
+    if ((status = spdhg_objective(ctx, nullptr, SPDHG_WHERE_DEVICE, o, stream))) goto done;
+    rep->objective[0] = o[2];
+  }
+  for (int ep = 0; ep < params->epochs; ++ep) {
+    spdhg_sample(ctx->params.seed, (uint64_t)ep * ipe, ipe, ctx->probs.data(), (int)ctx->probs.size(), seq.data());
+    if (cudaEventRecord(e0, s) != cudaSuccess) { status = fail(ctx, SPDHG_ERR_CUDA, "event record"); goto done; }
+    if ((status = spdhg_iterate(ctx, seq.data(), ipe, stream))) goto done;
+    if (cudaEventRecord(e1, s) != cudaSuccess) { status = fail(ctx, SPDHG_ERR_CUDA, "event record"); goto done; }
+    if (rep && rep->epoch_ms) {
+      float ms = 0.f;
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+      rep->epoch_ms[ep] = ms;
+    }
+    if (rep) {
+      rep->epochs_done = ep + 1;
+      rep->iterations_done = (int64_t)(ep + 1) * ipe;
+    }
+    if (every > 0 && (ep + 1) % every == 0) {
+      double o[3];
+      if ((status = spdhg_objective(ctx, nullptr, SPDHG_WHERE_DEVICE, o, stream))) goto done;
+      if (rep && rep->objective) rep->objective[ep + 1] = o[2];
+      if (!isfinite(o[2])) { status = fail(ctx, SPDHG_ERR_DIVERGED, "objective is not finite"); goto done; }
+    }
+  }
+  if (x_inout) status = copy_out(ctx, x_inout, ctx->x[ctx->xcur], ctx->N, where, s);
+  if (status == SPDHG_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) status = fail(ctx, SPDHG_ERR_CUDA, cudaGetErrorString(e));
+  }
+done:
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return status;
+}
+
+int spdhg_profile(spdhg_ctx* ctx, int enable) {
+  if (!ctx) return SPDHG_ERR_ARG;
+  for (auto& r : ctx->prof_pending) {
+    ctx->prof_pool.push_back(r.a);
+    ctx->prof_pool.push_back(r.b);
+  }
+  ctx->prof_pending.clear();
+  for (int k = 0; k < SPDHG_KERNEL_KINDS; ++k) {
+    ctx->prof_ms[k] = 0.0;
+    ctx->prof_n[k] = 0;
+  }
+  ctx->profiling = enable != 0;
+  return SPDHG_OK;
+}
+
+int spdhg_profile_read(spdhg_ctx* ctx, double* ms, int64_t* launches, int n) {
+  if (!ctx || n < 0 || n > SPDHG_KERNEL_KINDS) return SPDHG_ERR_ARG;
+  for (auto& r : ctx->prof_pending) {
+    CK(cudaEventSynchronize(r.b));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    ctx->prof_ms[r.kind] += t;
+    ctx->prof_n[r.kind] += 1;
+    ctx->prof_pool.push_back(r.a);
+    ctx->prof_pool.push_back(r.b);
+  }
+  ctx->prof_pending.clear();
+  for (int k = 0; k < n; ++k) {
+    if (ms) ms[k] = ctx->prof_ms[k];
+    if (launches) launches[k] = ctx->prof_n[k];
+  }
+  return SPDHG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// Internal declarations shared by the CUDA translation units of libspdhg.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/spdhg.h"
+
+namespace spdhg {
+
+constexpr int kMaxSeg = 32;       // segments held in the per-line shared tables
+constexpr int kMaxTaps = 4;       // slices an oblique LOR may cross inside one transaxial pixel
+constexpr int kMaxPlanesPerThread = 4;
+
+// Per-segment constants.  Plane q of segment g has its LOR mid-point at slab coordinate
+// f + q (in units of vz measured from the lower image face, so slab iz is [iz, iz+1)).
+struct SegDev {
+  int p0;      // first plane index of the segment in the sinogram
+  int n;       // planes in the segment
+  float f;     // (zmid0 - z_lo) / vz
+  float dz;    // z2 - z1 of the segment's LORs, mm
+};
+
+// Geometry passed by value to every kernel.
+struct DevGeom {
+  int nx, ny, nz;
+  float vx, vz;
+  float lox, loy;        // lower corner of the image box (x, y), mm
+  float inv_vx;
+  int R, V, P, m;        // radial bins, views, planes, subsets
+  int n_seg;
+  int taps;              // maximum slices a LOR crosses inside one pixel
+  int nr_max;            // maximum candidate radial bins per pixel and view
+  float d_radial, half_R, radius2;
+  const float2* view_cs; // (cos, sin) per view, exact zeros on the axes
+  const SegDev* seg;
+  const int* plane_seg;  // plane -> segment
+};
+
+// Views of subset i: i, i+m, ...  (subset < 0: all views).
+__host__ __device__ inline int subset_views(const DevGeom& g, int subset) {
+  return subset < 0 ? g.V : (g.V - subset + g.m - 1) / g.m;
+}
+__host__ __device__ inline int subset_view(const DevGeom& g, int subset, int l) {
+  return subset < 0 ? l : subset + l * g.m;
+}
+
+struct Ctx;
+
+// ---------------------------------------------------------------------------------------
+// projector launches (projector.cu)
+// ---------------------------------------------------------------------------------------
+enum FwdMode { FWD_PROJECT = 0, FWD_SIGMA = 1, FWD_DATA = 2 };
+enum BwdMode { BWD_OUT = 0, BWD_SENS = 1, BWD_UPDATE = 2 };
+
+struct FwdArgs {
+  const float* x;        // image
+  float* out;            // FWD_PROJECT: y (full sinogram); FWD_SIGMA: sigma (full sinogram)
+  const float* mult;     // may be null (ones)
+  // FWD_DATA
+  const float* b;
+  const float* r;
+  float* y;              // dual, full sinogram
+  float* wdy;            // subset-local mult * (y+ - y)
+  float gamma_rho;       // gamma * rho
+};
+
+struct BwdArgs {
+  const float* w;        // subset-local sinogram (mult already applied)
+  float* out;            // BWD_OUT: image (overwritten)
+  float* T;              // BWD_SENS: running min; BWD_UPDATE: step image
+  float sens_num;        // BWD_SENS: rho p_i / gamma
+  float* x;              // BWD_UPDATE
+  float* z;
+  float inv_p;
+};
+
+cudaError_t launch_forward(const DevGeom& g, int subset, int mode, const FwdArgs& a, cudaStream_t s);
+cudaError_t launch_backward(const DevGeom& g, int subset, int mode, const BwdArgs& a, cudaStream_t s);
+// w_local = mult * y over the bins of subset i (mult may be null)
+cudaError_t launch_gather_subset(const DevGeom& g, int subset, const float* y, const float* mult,
+                                 float* w_local, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------
+// prior (prior.cu)
+// ---------------------------------------------------------------------------------------
+struct PriorArgs {
+  int kind;              // SPDHG_PRIOR_TV / DTV / ATV
+  const float* x_in;
+  float* x_out;
+  const float* q_in;     // 3N
+  float* q_out;
+  float* z;
+  const float* T;
+  const float* side;     // dTV side image v
+  float sigma, alpha, inv_p, gamma_d, eta2;
+};
+cudaError_t launch_prior(const DevGeom& g, const PriorArgs& a, cudaStream_t s);
+
+struct TgvArgs {
+  int block;             // 0: A = (grad, -I), 1: A = (0, E)
+  const float* u_in; float* u_out;
+  const float* w_in; float* w_out;      // 3N each
+  const float* q_in; float* q_out;      // 3N (block 0) or 6N (block 1)
+  float* zu; float* zw;
+  const float* Tu; float Tw;
+  float sigma, alpha, inv_p;
+};
+cudaError_t launch_tgv(const DevGeom& g, const TgvArgs& a, cudaStream_t s);
+// data iteration for TGV also steps w: w -= Tw * zbar_w with zbar_w = zw (no new w-dual change)
+cudaError_t launch_w_step(const DevGeom& g, float* w, const float* zw, float Tw, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------
+// objective (objective.cu)
+// ---------------------------------------------------------------------------------------
+cudaError_t launch_data_term(const float* ax, const float* b, const float* r, int64_t M,
+                             double* partial, int nblocks, double* out, cudaStream_t s);
+cudaError_t launch_prior_term(const DevGeom& g, int kind, const float* x, const float* w,
+                              const float* side, float gamma_d, float eta2, double* partial,
+                              int nblocks, double* out, cudaStream_t s);
+cudaError_t launch_side_max_grad(const DevGeom& g, const float* side, double* partial, int nblocks,
+                                 double* out, cudaStream_t s);
+
+}  // namespace spdhg
+
+// The opaque context of the C ABI.
+struct spdhg_ctx {
+  spdhg_geometry geom{};
+  std::vector<int> seg_n;
+  std::vector<double> seg_zmid0, seg_dzmid, seg_dz;
+  spdhg::DevGeom dg{};
+  int64_t N = 0, M = 0, max_subset_bins = 0;
+  int device = 0;
+  // device tables
+  float2* d_view_cs = nullptr;
+  spdhg::SegDev* d_seg = nullptr;
+  int* d_plane_seg = nullptr;
+  // data
+  float *b = nullptr, *r = nullptr, *mult = nullptr, *side = nullptr;
+  bool has_data = false, has_mult = false, has_side = false;
+  // state
+  float* x[2] = {nullptr, nullptr};
+  int xcur = 0;
+  float *z = nullptr, *T = nullptr, *y = nullptr, *wdy = nullptr;
+  float* q[2] = {nullptr, nullptr};
+  int qcur = 0;
+  // TGV
+  float* w[2] = {nullptr, nullptr};
+  int wcur = 0;
+  float* zw = nullptr;
+  float* q2[2] = {nullptr, nullptr};
+  int q2cur = 0;
+  float Tw = 0.f;
+  // scratch
+  float* tmp_sino = nullptr;   // M floats (objective, sigma export)
+  float* tmp_img = nullptr;    // N floats (objective of a host image)
+  double* red = nullptr;       // FP64 partial sums
+  double* red_out = nullptr;   // FP64 results (4)
+  int red_blocks = 1024;
+  // parameters of the last setup
+  bool is_setup = false;
+  spdhg_params params{};
+  std::vector<double> probs;
+  std::vector<float> sigma_prior;
+  double eta2 = 0.0;
+  int64_t iterations = 0;
+  std::string err;
+  // per-launch profiler
+  bool profiling = false;
+  struct ProfRec { int kind; cudaEvent_t a, b; };
+  std::vector<ProfRec> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  double prof_ms[SPDHG_KERNEL_KINDS] = {0, 0, 0, 0, 0};
+  int64_t prof_n[SPDHG_KERNEL_KINDS] = {0, 0, 0, 0, 0};
+};
