@@ -200,61 +200,82 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   ctx->M = (int64_t)g.n_views * g.n_radial * P;
   ctx->max_subset_bins = (int64_t)((g.n_views + g.n_subsets - 1) / g.n_subsets) * g.n_radial * P;
 
-  // device tables
+  // device tables (FP64 on the host, stored as double-float pairs hi + lo)
   const double pi = 3.14159265358979323846;
-  std::vector<float2> cs(g.n_views);
-  for (int v = 0; v < g.n_views; ++v) {
-    double c = cos(pi * v / g.n_views), s = sin(pi * v / g.n_views);
+  auto split = [](double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+  };
+  const int R = g.n_radial, V = g.n_views, S = g.n_segments;
+  std::vector<float4> view(V), rad(R), rs((size_t)R * S);
+  for (int v = 0; v < V; ++v) {
+    double c = cos(pi * v / V), sn = sin(pi * v / V);
     if (fabs(c) < 1e-12) c = 0.0;
-    if (fabs(s) < 1e-12) s = 0.0;
-    cs[v] = make_float2((float)c, (float)s);
+    if (fabs(sn) < 1e-12) sn = 0.0;
+    float4 t;
+    split(c, t.x, t.y);
+    split(sn, t.z, t.w);
+    view[v] = t;
+  }
+  for (int r = 0; r < R; ++r) {
+    const double s = (r - 0.5 * (R - 1)) * g.d_radial;
+    const double h = sqrt(g.radius * g.radius - s * s);
+    float4 t;
+    split(s / g.vx, t.x, t.y);
+    split(h / g.vx, t.z, t.w);
+    rad[r] = t;
+    for (int k = 0; k < S; ++k) {
+      const double slope = g.seg_dz[k] / (2.0 * h);  // dz/dt of the LOR
+      float4 u;
+      split(slope * g.vx / g.vz, u.x, u.y);          // slab units per pixel unit of t
+      u.z = (float)sqrt(1.0 + slope * slope);        // 3-D length per transaxial length
+      u.w = 0.f;
+      rs[(size_t)r * S + k] = u;
+    }
   }
   const double loz = -0.5 * g.nz * g.vz;
-  std::vector<SegDev> seg(g.n_segments);
+  std::vector<SegDev> seg(S);
   std::vector<int> plane_seg(P);
   int p0 = 0;
-  for (int k = 0; k < g.n_segments; ++k) {
+  for (int k = 0; k < S; ++k) {
     seg[k].p0 = p0;
     seg[k].n = g.seg_n[k];
-    seg[k].f = (float)((g.seg_zmid0[k] - loz) / g.vz);
-    seg[k].dz = (float)g.seg_dz[k];
+    split((g.seg_zmid0[k] - loz) / g.vz, seg[k].f_hi, seg[k].f_lo);
     for (int q = 0; q < g.seg_n[k]; ++q) plane_seg[p0 + q] = k;
     p0 += g.seg_n[k];
   }
   auto cleanup_fail = [&](cudaError_t e) {
-    std::string msg = std::string("device table upload failed: ") + cudaGetErrorString(e);
     spdhg_destroy(ctx);
-    (void)msg;
     return e == cudaErrorMemoryAllocation ? SPDHG_ERR_OOM : SPDHG_ERR_CUDA;
   };
   cudaError_t e;
-  if ((e = cudaMalloc(&ctx->d_view_cs, sizeof(float2) * g.n_views)) != cudaSuccess) return cleanup_fail(e);
-  if ((e = cudaMalloc(&ctx->d_seg, sizeof(SegDev) * g.n_segments)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMalloc(&ctx->d_view, sizeof(float4) * V)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMalloc(&ctx->d_rad, sizeof(float4) * R)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMalloc(&ctx->d_rs, sizeof(float4) * R * S)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMalloc(&ctx->d_seg, sizeof(SegDev) * S)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMalloc(&ctx->d_plane_seg, sizeof(int) * P)) != cudaSuccess) return cleanup_fail(e);
-  if ((e = cudaMemcpy(ctx->d_view_cs, cs.data(), sizeof(float2) * g.n_views, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
-  if ((e = cudaMemcpy(ctx->d_seg, seg.data(), sizeof(SegDev) * g.n_segments, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMemcpy(ctx->d_view, view.data(), sizeof(float4) * V, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMemcpy(ctx->d_rad, rad.data(), sizeof(float4) * R, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMemcpy(ctx->d_rs, rs.data(), sizeof(float4) * R * S, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMemcpy(ctx->d_seg, seg.data(), sizeof(SegDev) * S, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_plane_seg, plane_seg.data(), sizeof(int) * P, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
 
   DevGeom& d = ctx->dg;
   d.nx = g.nx;
   d.ny = g.ny;
   d.nz = g.nz;
-  d.vx = (float)g.vx;
-  d.vz = (float)g.vz;
-  d.lox = (float)(-0.5 * g.nx * g.vx);
-  d.loy = (float)(-0.5 * g.ny * g.vy);
-  d.inv_vx = (float)(1.0 / g.vx);
-  d.R = g.n_radial;
-  d.V = g.n_views;
+  d.R = R;
+  d.V = V;
   d.P = P;
   d.m = g.n_subsets;
-  d.n_seg = g.n_segments;
+  d.n_seg = S;
   d.taps = taps;
   d.nr_max = nr_max;
-  d.d_radial = (float)g.d_radial;
-  d.half_R = (float)(0.5 * (g.n_radial - 1));
-  d.radius2 = (float)(g.radius * g.radius);
-  d.view_cs = ctx->d_view_cs;
+  d.half_R = (float)(0.5 * (R - 1));
+  d.inv_drp = (float)(g.vx / g.d_radial);
+  d.view = ctx->d_view;
+  d.rad = ctx->d_rad;
+  d.rs = ctx->d_rs;
   d.seg = ctx->d_seg;
   d.plane_seg = ctx->d_plane_seg;
   *out = ctx;
@@ -263,7 +284,7 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
 
 void spdhg_destroy(spdhg_ctx* ctx) {
   if (!ctx) return;
-  void* ptrs[] = {ctx->d_view_cs, ctx->d_seg, ctx->d_plane_seg, ctx->b, ctx->r, ctx->mult, ctx->side,
+  void* ptrs[] = {ctx->d_view, ctx->d_rad, ctx->d_rs, ctx->d_seg, ctx->d_plane_seg, ctx->b, ctx->r, ctx->mult, ctx->side,
                   ctx->x[0], ctx->x[1], ctx->z, ctx->T, ctx->y, ctx->wdy, ctx->q[0], ctx->q[1],
                   ctx->w[0], ctx->w[1], ctx->zw, ctx->q2[0], ctx->q2[1], ctx->tmp_sino, ctx->tmp_img,
                   ctx->red, ctx->red_out};

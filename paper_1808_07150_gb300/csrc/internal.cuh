@@ -16,26 +16,28 @@ constexpr int kMaxTaps = 4;       // slices an oblique LOR may cross inside one 
 constexpr int kMaxPlanesPerThread = 4;
 
 // Per-segment constants.  Plane q of segment g has its LOR mid-point at slab coordinate
-// f + q (in units of vz measured from the lower image face, so slab iz is [iz, iz+1)).
+// f + q (in units of vz measured from the lower image face, so slab iz is [iz, iz+1)); f is
+// held as a double-float pair f_hi + f_lo.
 struct SegDev {
   int p0;      // first plane index of the segment in the sinogram
   int n;       // planes in the segment
-  float f;     // (zmid0 - z_lo) / vz
-  float dz;    // z2 - z1 of the segment's LORs, mm
+  float f_hi, f_lo;
 };
 
-// Geometry passed by value to every kernel.
+// Geometry passed by value to every kernel.  Transaxial quantities are in pixel units (mm / vx);
+// every table entry that enters a length is a double-float pair (hi + lo) so that the position of
+// a LOR relative to a pixel is resolved far below FP32 rounding of the absolute coordinates.
 struct DevGeom {
   int nx, ny, nz;
-  float vx, vz;
-  float lox, loy;        // lower corner of the image box (x, y), mm
-  float inv_vx;
   int R, V, P, m;        // radial bins, views, planes, subsets
   int n_seg;
   int taps;              // maximum slices a LOR crosses inside one pixel
   int nr_max;            // maximum candidate radial bins per pixel and view
-  float d_radial, half_R, radius2;
-  const float2* view_cs; // (cos, sin) per view, exact zeros on the axes
+  float half_R;          // (R - 1) / 2
+  float inv_drp;         // vx / d_radial: radial bins per pixel unit
+  const float4* view;    // per view: cos_hi, cos_lo, sin_hi, sin_lo (exact zeros on the axes)
+  const float4* rad;     // per radial bin: s_hi, s_lo, h_hi, h_lo (s = signed offset, h = half chord)
+  const float4* rs;      // per (radial bin, segment): kappa_hi, kappa_lo, len_scale, 0
   const SegDev* seg;
   const int* plane_seg;  // plane -> segment
 };
@@ -135,7 +137,9 @@ struct spdhg_ctx {
   int64_t N = 0, M = 0, max_subset_bins = 0;
   int device = 0;
   // device tables
-  float2* d_view_cs = nullptr;
+  float4* d_view = nullptr;
+  float4* d_rad = nullptr;
+  float4* d_rs = nullptr;
   spdhg::SegDev* d_seg = nullptr;
   int* d_plane_seg = nullptr;
   // data

@@ -17,96 +17,122 @@
 
 namespace spdhg {
 
-struct Line {
-  float ox, oy, dx, dy, inv_dx, inv_dy, h;
-};
-
-// Transaxial line of (view v, radial bin r): P(t) = (ox + t dx, oy + t dy), t in [-h, h].
-__device__ __forceinline__ Line make_line(const DevGeom& g, int v, int r) {
-  const float2 cs = g.view_cs[v];
-  Line L;
-  const float s = __fmul_rn(__fsub_rn((float)r, g.half_R), g.d_radial);
-  L.ox = __fmul_rn(s, cs.x);
-  L.oy = __fmul_rn(s, cs.y);
-  L.dx = -cs.y;
-  L.dy = cs.x;
-  L.inv_dx = (L.dx != 0.f) ? __frcp_rn(L.dx) : 0.f;
-  L.inv_dy = (L.dy != 0.f) ? __frcp_rn(L.dy) : 0.f;
-  L.h = __fsqrt_rn(__fsub_rn(g.radius2, __fmul_rn(s, s)));
-  return L;
+// Error-free transformations (Knuth two-sum, FMA two-product): a + b = s + e, a * b = p + e.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
 }
 
-__device__ __forceinline__ float grid_x(const DevGeom& g, int i) { return __fmaf_rn((float)i, g.vx, g.lox); }
-__device__ __forceinline__ float grid_y(const DevGeom& g, int i) { return __fmaf_rn((float)i, g.vx, g.loy); }
+// Transaxial line of (view v, radial bin r) in pixel units: the points X n_perp with
+// X . (c, s) = s_r, parameter t along (-s, c), t in [-h, h]  (all as double-float pairs).
+struct Line {
+  float c_hi, c_lo, s_hi, s_lo;
+  float sp_hi, sp_lo, h_hi, h_lo;
+};
 
-// [ta, tb] = {t in [-h, h] : P(t) in pixel (ix, iy)}; false if empty.  A line lying in a grid
-// line belongs to the pixel whose lower edge holds it.
-__device__ __forceinline__ bool pixel_interval(const DevGeom& g, const Line& L, int ix, int iy,
-                                               float& ta, float& tb) {
-  float lo = -L.h, hi = L.h;
-  const float X0 = grid_x(g, ix), X1 = grid_x(g, ix + 1);
-  if (L.dx == 0.f) {
-    if (!(X0 <= L.ox && L.ox < X1)) return false;
+__device__ __forceinline__ Line make_line(const DevGeom& g, int v, int r) {
+  const float4 a = g.view[v];
+  const float4 b = g.rad[r];
+  return Line{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+}
+
+// Intersection of a line with pixel (ix, iy), expressed relative to the foot point of the
+// pixel centre on the line: t in tc + [ua, ub], tc = tch + tcl.  The offset of the line from
+// the pixel centre and tc are evaluated with error-free transformations, so [ua, ub] is
+// resolved to FP32 precision of quantities of order one pixel.  A line lying in a grid line
+// belongs to the pixel whose lower edge holds it.
+struct PixInt {
+  float ua, ub, tch, tcl;
+};
+
+__device__ __forceinline__ bool pixel_interval(const DevGeom& g, const Line& L, int ix, int iy, PixInt& out) {
+  const float Xc = (float)ix + 0.5f - 0.5f * (float)g.nx;  // pixel centre (exact)
+  const float Yc = (float)iy + 0.5f - 0.5f * (float)g.ny;
+  float p1, e1, p2, e2, S, eS, D, eD;
+  // delta = Xc c + Yc s - s_r: signed distance of the pixel centre from the line
+  two_prod(Xc, L.c_hi, p1, e1);
+  two_prod(Yc, L.s_hi, p2, e2);
+  two_sum(p1, p2, S, eS);
+  two_sum(S, -L.sp_hi, D, eD);
+  const float delta = __fadd_rn(D, __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(eS, eD)),
+                                              __fsub_rn(__fmaf_rn(Xc, L.c_lo, __fmul_rn(Yc, L.s_lo)), L.sp_lo)));
+  // tc = Yc c - Xc s: line parameter of the foot point
+  two_prod(Yc, L.c_hi, p1, e1);
+  two_prod(-Xc, L.s_hi, p2, e2);
+  two_sum(p1, p2, S, eS);
+  two_sum(S, __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), eS), __fsub_rn(__fmul_rn(Yc, L.c_lo), __fmul_rn(Xc, L.s_lo))),
+          out.tch, out.tcl);
+  // segment ends t = -h, h relative to tc
+  float lo = __fadd_rn(__fsub_rn(-L.h_hi, out.tch), __fsub_rn(-L.h_lo, out.tcl));
+  float hi = __fadd_rn(__fsub_rn(L.h_hi, out.tch), __fsub_rn(L.h_lo, out.tcl));
+  const float ex = __fmul_rn(-delta, L.c_hi), ey = __fmul_rn(-delta, L.s_hi);  // foot point - centre
+  const float dx = -L.s_hi, dy = L.c_hi;
+  if (dx == 0.f) {
+    if (!(ex >= -0.5f && ex < 0.5f)) return false;
   } else {
-    const float t0 = __fmul_rn(__fsub_rn(X0, L.ox), L.inv_dx);
-    const float t1 = __fmul_rn(__fsub_rn(X1, L.ox), L.inv_dx);
-    lo = fmaxf(lo, fminf(t0, t1));
-    hi = fminf(hi, fmaxf(t0, t1));
+    const float u1 = __fdiv_rn(__fsub_rn(-0.5f, ex), dx), u2 = __fdiv_rn(__fsub_rn(0.5f, ex), dx);
+    lo = fmaxf(lo, fminf(u1, u2));
+    hi = fminf(hi, fmaxf(u1, u2));
   }
-  const float Y0 = grid_y(g, iy), Y1 = grid_y(g, iy + 1);
-  if (L.dy == 0.f) {
-    if (!(Y0 <= L.oy && L.oy < Y1)) return false;
+  if (dy == 0.f) {
+    if (!(ey >= -0.5f && ey < 0.5f)) return false;
   } else {
-    const float t0 = __fmul_rn(__fsub_rn(Y0, L.oy), L.inv_dy);
-    const float t1 = __fmul_rn(__fsub_rn(Y1, L.oy), L.inv_dy);
-    lo = fmaxf(lo, fminf(t0, t1));
-    hi = fminf(hi, fmaxf(t0, t1));
+    const float u1 = __fdiv_rn(__fsub_rn(-0.5f, ey), dy), u2 = __fdiv_rn(__fsub_rn(0.5f, ey), dy);
+    lo = fmaxf(lo, fminf(u1, u2));
+    hi = fminf(hi, fmaxf(u1, u2));
   }
-  ta = lo;
-  tb = hi;
+  out.ua = lo;
+  out.ub = hi;
   return hi > lo;
 }
 
-// Axial constants of a LOR line for one segment: slab coordinate zeta(t) = f + j + kappa t.
-struct SegLine {
-  float f, kappa, inv_kappa, scale;
-};
-
-__device__ __forceinline__ SegLine seg_line(const DevGeom& g, const Line& L, int gi) {
-  const SegDev sd = g.seg[gi];
-  const float slope = __fdiv_rn(sd.dz, __fmul_rn(2.f, L.h));
-  SegLine S;
-  S.f = sd.f;
-  S.kappa = __fdiv_rn(slope, g.vz);
-  S.inv_kappa = (S.kappa != 0.f) ? __frcp_rn(S.kappa) : 0.f;
-  const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(L.dx, L.dx), __fmul_rn(L.dy, L.dy)), __fmul_rn(slope, slope));
-  S.scale = __fdiv_rn(__fsqrt_rn(n2), g.vx);  // |dP/dt| in voxel units
-  return S;
-}
-
-// Lengths (voxel units) of the plane-q LOR in slabs iz = q - (j0 + k), k < NT, for the pixel
-// interval [ta, tb].  Returns j0.
+// Lengths (voxel units) of the plane-q LOR of segment gi in slabs iz = q - (j0 + k), k < NT,
+// inside the pixel interval I.  The LOR's slab coordinate at the foot point,
+// zeta_c = f + kappa tc, is split exactly into an integer n0 and a fraction in [0, 1); the
+// crossings are then solved in local quantities of order one.  Returns j0.
 template <int NT>
-__device__ __forceinline__ int segment_taps(const SegLine& S, float ta, float tb, float* Lk) {
-  if (S.kappa == 0.f) {
-    const int j0 = -(int)floorf(S.f);  // f + j0 in [0, 1): the slab holding the LOR
-    Lk[0] = __fmul_rn(__fsub_rn(tb, ta), S.scale);
+__device__ __forceinline__ int segment_taps(const DevGeom& g, int r, int gi, const PixInt& I, float* Lk) {
+  const float4 rs = g.rs[r * g.n_seg + gi];
+  const SegDev sd = g.seg[gi];
+  const float kh = rs.x, kl = rs.y, scale = rs.z;
+  float p, e, s1, e1;
+  two_prod(kh, I.tch, p, e);
+  e = __fadd_rn(e, __fmaf_rn(kh, I.tcl, __fmul_rn(kl, I.tch)));
+  two_sum(sd.f_hi, p, s1, e1);
+  float n0 = floorf(s1);
+  float frac = __fadd_rn(__fsub_rn(s1, n0), __fadd_rn(__fadd_rn(e1, e), sd.f_lo));
+  if (frac >= 1.f) {
+    frac -= 1.f;
+    n0 += 1.f;
+  } else if (frac < 0.f) {
+    frac += 1.f;
+    n0 -= 1.f;
+  }
+  const int in0 = (int)n0;
+  if (kh == 0.f) {
+    Lk[0] = __fmul_rn(__fsub_rn(I.ub, I.ua), scale);
 #pragma unroll
     for (int k = 1; k < NT; ++k) Lk[k] = 0.f;
-    return j0;
+    return -in0;  // frac in [0, 1): the LOR stays in one slab
   }
-  const float ka = __fmul_rn(S.kappa, ta), kb = __fmul_rn(S.kappa, tb);
-  const float B = __fadd_rn(S.f, fmaxf(ka, kb));
-  const int j0 = (int)floorf(-B) + 1;  // smallest j with f + j + max(kappa t) > 0
+  const float ka = __fmul_rn(kh, I.ua), kb = __fmul_rn(kh, I.ub);
+  const float B = __fadd_rn(frac, fmaxf(ka, kb));
+  const int j0l = (int)floorf(-B) + 1;  // smallest local j with frac + j + max(kappa u) > 0
+  const float inv_k = __frcp_rn(kh);
 #pragma unroll
   for (int k = 0; k < NT; ++k) {
-    const float u0 = -__fadd_rn(S.f, (float)(j0 + k));  // zeta = 0  at  t = u0 / kappa
-    const float u1 = __fadd_rn(u0, 1.f);               // zeta = 1  at  t = u1 / kappa
-    const float t0 = __fmul_rn(u0, S.inv_kappa), t1 = __fmul_rn(u1, S.inv_kappa);
-    const float lo = fmaxf(ta, fminf(t0, t1)), hi = fminf(tb, fmaxf(t0, t1));
-    Lk[k] = hi > lo ? __fmul_rn(__fsub_rn(hi, lo), S.scale) : 0.f;
+    const float u0 = -__fadd_rn(frac, (float)(j0l + k));  // zeta = 0 at u = u0 / kappa
+    const float u1 = __fadd_rn(u0, 1.f);                  // zeta = 1 at u = u1 / kappa
+    const float t0 = __fmul_rn(u0, inv_k), t1 = __fmul_rn(u1, inv_k);
+    const float lo = fmaxf(I.ua, fminf(t0, t1)), hi = fminf(I.ub, fmaxf(t0, t1));
+    Lk[k] = hi > lo ? __fmul_rn(__fsub_rn(hi, lo), scale) : 0.f;
   }
-  return j0;
+  return j0l - in0;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -114,65 +140,61 @@ __device__ __forceinline__ int segment_taps(const SegLine& S, float ta, float tb
 // ---------------------------------------------------------------------------------------
 
 struct Entry {
-  int col;  // iy * nx + ix, or -1
-  float ta, tb;
+  int col;  // iy * nx + ix
+  PixInt I;
 };
 
-// The (at most two) pixels of `row` along the dominant axis crossed by the line.
-__device__ __forceinline__ void row_entries(const DevGeom& g, const Line& L, bool ydom, int row,
-                                            Entry& e0, Entry& e1) {
-  e0.col = -1;
-  e1.col = -1;
-  const float inv_d = ydom ? L.inv_dy : L.inv_dx;
-  const float o = ydom ? L.oy : L.ox;
-  const float G0 = ydom ? grid_y(g, row) : grid_x(g, row);
-  const float G1 = ydom ? grid_y(g, row + 1) : grid_x(g, row + 1);
-  const float t0 = __fmul_rn(__fsub_rn(G0, o), inv_d), t1 = __fmul_rn(__fsub_rn(G1, o), inv_d);
-  const float tlo = fmaxf(-L.h, fminf(t0, t1)), thi = fminf(L.h, fmaxf(t0, t1));
-  if (!(thi > tlo)) return;
-  const float oc = ydom ? L.ox : L.oy;   // coordinate across the row
-  const float dc = ydom ? L.dx : L.dy;
-  const float lo = ydom ? g.lox : g.loy;
-  const int nc = ydom ? g.nx : g.ny;
-  int c0;
-  if (dc == 0.f) {
-    c0 = (int)floorf(__fmul_rn(__fsub_rn(oc, lo), g.inv_vx));
-    const float C0 = __fmaf_rn((float)c0, g.vx, lo), C1 = __fmaf_rn((float)(c0 + 1), g.vx, lo);
-    if (C0 > oc) --c0;
-    else if (C1 <= oc) ++c0;
-  } else {
-    const float ca = __fmaf_rn(tlo, dc, oc), cb = __fmaf_rn(thi, dc, oc);
-    c0 = (int)floorf(__fmul_rn(__fsub_rn(fminf(ca, cb), lo), g.inv_vx));
+constexpr int kCandPerRow = 4;
+
+// Pixels of `row` (along the dominant axis of the line) that the line crosses.  Candidates come
+// from approximate arithmetic (one pixel of margin on each side); pixel_interval decides exactly.
+__device__ __forceinline__ int row_entries(const DevGeom& g, const Line& L, bool ydom, int row, Entry* e) {
+  const float c = L.c_hi, s = L.s_hi, sp = L.sp_hi, h = L.h_hi;
+  float t0, t1;
+  if (ydom) {  // y in [Y0, Y0 + 1);  y(t) = sp s + t c
+    const float Y0 = (float)row - 0.5f * (float)g.ny;
+    t0 = (Y0 - sp * s) / c;
+    t1 = (Y0 + 1.f - sp * s) / c;
+  } else {     // x in [X0, X0 + 1);  x(t) = sp c - t s
+    const float X0 = (float)row - 0.5f * (float)g.nx;
+    t0 = (sp * c - X0) / s;
+    t1 = (sp * c - X0 - 1.f) / s;
   }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int c = c0 + k;
-    if (c < 0 || c >= nc) continue;
-    const int ix = ydom ? c : row, iy = ydom ? row : c;
-    float ta, tb;
-    if (pixel_interval(g, L, ix, iy, ta, tb)) {
-      Entry& e = k ? e1 : e0;
-      e.col = iy * g.nx + ix;
-      e.ta = ta;
-      e.tb = tb;
+  const float tlo = fmaxf(fminf(t0, t1), -h - 1e-2f), thi = fminf(fmaxf(t0, t1), h + 1e-2f);
+  if (thi < tlo) return 0;
+  const float ca = ydom ? sp * c - tlo * s : sp * s + tlo * c;
+  const float cb = ydom ? sp * c - thi * s : sp * s + thi * c;
+  const float half = 0.5f * (float)(ydom ? g.nx : g.ny);
+  const int nc = ydom ? g.nx : g.ny;
+  const int cmin = max((int)floorf(fminf(ca, cb) + half) - 1, 0);
+  const int cmax = min((int)floorf(fmaxf(ca, cb) + half) + 1, nc - 1);
+  int n = 0;
+  for (int cc = cmin; cc <= cmax && n < kCandPerRow; ++cc) {
+    const int ix = ydom ? cc : row, iy = ydom ? row : cc;
+    PixInt I;
+    if (pixel_interval(g, L, ix, iy, I)) {
+      e[n].col = iy * g.nx + ix;
+      e[n].I = I;
+      ++n;
     }
   }
+  return n;
 }
 
 template <int NT, int PPT, int MODE>
 __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc, FwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ SegLine sl[kMaxSeg];
-  const int n_ent = 2 * rpc;
+  __shared__ int warp_tot[2];
+  __shared__ int n_ent_sh;
+  const int cap = kCandPerRow * rpc;
   Entry* ent = reinterpret_cast<Entry*>(smem);
-  int* tapJ = reinterpret_cast<int*>(ent + n_ent);
-  float* tapL = reinterpret_cast<float*>(tapJ + g.n_seg * n_ent);
+  int* tapJ = reinterpret_cast<int*>(ent + cap);
+  float* tapL = reinterpret_cast<float*>(tapJ + g.n_seg * cap);
 
   const int line = blockIdx.x;
   const int l = line / g.R, r = line - (line / g.R) * g.R;
   const int v = subset_view(g, subset, l);
   const Line L = make_line(g, v, r);
-  if (threadIdx.x < g.n_seg) sl[threadIdx.x] = seg_line(g, L, threadIdx.x);
 
   int pseg[PPT], pq[PPT];
   float acc[PPT], chord[PPT];
@@ -190,49 +212,56 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc,
       pq[k] = 0;
     }
   }
-  const bool ydom = fabsf(L.dy) >= fabsf(L.dx);
+  const bool ydom = fabsf(L.c_hi) >= fabsf(L.s_hi);  // |dy| >= |dx|: walk the rows of y
   const int nrows = ydom ? g.ny : g.nx;
   const int nz = g.nz;
-  __syncthreads();
 
   for (int row0 = 0; row0 < nrows; row0 += rpc) {
-    for (int t = threadIdx.x; t < rpc; t += blockDim.x) {
-      Entry e0, e1;
-      e0.col = -1;
-      e1.col = -1;
-      if (row0 + t < nrows) row_entries(g, L, ydom, row0 + t, e0, e1);
-      ent[2 * t] = e0;
-      ent[2 * t + 1] = e1;
+    // 1. rows -> exact pixel intervals, compacted with a two-warp prefix sum (rpc <= 64)
+    Entry loc[kCandPerRow];
+    int cnt = 0;
+    if (threadIdx.x < rpc && row0 + (int)threadIdx.x < nrows) cnt = row_entries(g, L, ydom, row0 + threadIdx.x, loc);
+    int incl = 0;
+    if (threadIdx.x < 64) {
+      const int lane = threadIdx.x & 31;
+      incl = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (lane == 31) warp_tot[threadIdx.x >> 5] = incl;
     }
     __syncthreads();
+    if (threadIdx.x < 64) {
+      const int off = incl - cnt + (threadIdx.x >= 32 ? warp_tot[0] : 0);
+      for (int k = 0; k < cnt; ++k) ent[off + k] = loc[k];
+      if (threadIdx.x == 0) n_ent_sh = warp_tot[0] + (rpc > 32 ? warp_tot[1] : 0);
+    }
+    __syncthreads();
+    const int n_ent = n_ent_sh;
+    // 2. axial taps of every (entry, segment)
     for (int it = threadIdx.x; it < g.n_seg * n_ent; it += blockDim.x) {
       const int gi = it / n_ent, e = it - gi * n_ent;
-      const Entry en = ent[e];
       float Lk[NT];
-      int j0 = 0;
-      if (en.col >= 0) {
-        j0 = segment_taps<NT>(sl[gi], en.ta, en.tb, Lk);
-      } else {
+      const int j0 = segment_taps<NT>(g, r, gi, ent[e].I, Lk);
+      const int slot = gi * cap + e;
+      tapJ[slot] = j0;
 #pragma unroll
-        for (int k = 0; k < NT; ++k) Lk[k] = 0.f;
-      }
-      tapJ[it] = j0;
-#pragma unroll
-      for (int k = 0; k < NT; ++k) tapL[it * NT + k] = Lk[k];
+      for (int k = 0; k < NT; ++k) tapL[slot * NT + k] = Lk[k];
     }
     __syncthreads();
+    // 3. accumulate the planes of this thread over the entries
     for (int e = 0; e < n_ent; ++e) {
-      const int col = ent[e].col;
-      if (col < 0) continue;
-      const float* __restrict__ xc = a.x + (size_t)col * nz;
+      const float* __restrict__ xc = a.x + (size_t)ent[e].col * nz;
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         if (pseg[k] < 0) continue;
-        const int it = pseg[k] * n_ent + e;
-        const int iz = pq[k] - tapJ[it];
+        const int slot = pseg[k] * cap + e;
+        const int iz = pq[k] - tapJ[slot];
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-          const float Lt = tapL[it * NT + t];
+          const float Lt = tapL[slot * NT + t];
           const int izt = iz - t;
           if (izt >= 0 && izt < nz) {
             acc[k] = fmaf(Lt, __ldg(xc + izt), acc[k]);
@@ -286,61 +315,75 @@ struct Item {
   float L[NT];
 };
 
+struct PixItem {
+  int l, r;  // view (subset-local) and radial bin; r < 0: no intersection
+  PixInt I;
+};
+
 template <int NT, int MODE>
 __global__ void __launch_bounds__(256) k_backward(DevGeom g, int subset, int tpc, int cpb, int vchunk,
                                                   BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int per_view = g.nr_max * g.n_seg;
-  const int items_per_col = vchunk * per_view;
-  Item<NT>* items = reinterpret_cast<Item<NT>*>(smem) + (threadIdx.x / tpc) * items_per_col;
+  const int n_pix = vchunk * g.nr_max;
+  const int items_per_col = n_pix * g.n_seg;
+  const int cb = threadIdx.x / tpc;
+  PixItem* pix = reinterpret_cast<PixItem*>(smem) + cb * n_pix;
+  Item<NT>* items = reinterpret_cast<Item<NT>*>(reinterpret_cast<PixItem*>(smem) + cpb * n_pix) + cb * items_per_col;
   const int tz = threadIdx.x % tpc;
-  const int col = blockIdx.x * cpb + threadIdx.x / tpc;
+  const int col = blockIdx.x * cpb + cb;
   const bool live = col < g.nx * g.ny;
   const int iy = live ? col / g.nx : 0, ix = live ? col - iy * g.nx : 0;
   const int nviews = subset_views(g, subset);
-  const float xc = __fmaf_rn((float)ix + 0.5f, g.vx, g.lox);
-  const float yc = __fmaf_rn((float)iy + 0.5f, g.vx, g.loy);
-  const float inv_dr = 1.f / g.d_radial;
+  const float Xc = (float)ix + 0.5f - 0.5f * (float)g.nx;
+  const float Yc = (float)iy + 0.5f - 0.5f * (float)g.ny;
   const int nz = g.nz;
   float acc = 0.f;  // tpc >= nz: one voxel per thread
 
   for (int l0 = 0; l0 < nviews; l0 += vchunk) {
     const int nv = min(vchunk, nviews - l0);
-    for (int it = tz; it < nv * per_view; it += tpc) {
-      const int gi = it % g.n_seg;
-      const int rest = it / g.n_seg;
-      const int ri = rest % g.nr_max;
-      const int l = l0 + rest / g.nr_max;
+    // 1. (view, radial bin) pairs of the pixel footprint -> exact pixel intervals
+    for (int it = tz; it < nv * g.nr_max; it += tpc) {
+      const int l = l0 + it / g.nr_max, ri = it % g.nr_max;
+      PixItem P;
+      P.l = l;
+      P.r = -1;
+      if (live) {
+        const int v = subset_view(g, subset, l);
+        const float4 cs = g.view[v];
+        const float sc = Xc * cs.x + Yc * cs.z;
+        const float hw = 0.5f * (fabsf(cs.x) + fabsf(cs.z));
+        const int rlo = (int)ceilf((sc - hw) * g.inv_drp + g.half_R) - 1;
+        const int rhi = (int)floorf((sc + hw) * g.inv_drp + g.half_R) + 1;
+        const int r = rlo + ri;
+        if (r >= 0 && r < g.R && r <= rhi) {
+          const Line L = make_line(g, v, r);
+          if (pixel_interval(g, L, ix, iy, P.I)) P.r = r;
+        }
+      }
+      pix[it] = P;
+    }
+    __syncthreads();
+    // 2. axial taps per (pair, segment)
+    for (int it = tz; it < nv * g.nr_max * g.n_seg; it += tpc) {
+      const int pi = it / g.n_seg, gi = it - pi * g.n_seg;
+      const PixItem P = pix[pi];
       Item<NT> I;
       I.n = 0;
       I.base = 0;
       I.j0 = 0;
 #pragma unroll
       for (int k = 0; k < NT; ++k) I.L[k] = 0.f;
-      if (live) {
-        const int v = subset_view(g, subset, l);
-        const float2 cs = g.view_cs[v];
-        const float sc = xc * cs.x + yc * cs.y;
-        const float half = 0.5f * g.vx * (fabsf(cs.x) + fabsf(cs.y));
-        const int rlo = (int)ceilf((sc - half) * inv_dr + g.half_R) - 1;
-        const int rhi = (int)floorf((sc + half) * inv_dr + g.half_R) + 1;
-        const int r = rlo + ri;
-        if (r >= 0 && r < g.R && r <= rhi) {
-          const Line L = make_line(g, v, r);
-          float ta, tb;
-          if (pixel_interval(g, L, ix, iy, ta, tb)) {
-            const SegLine S = seg_line(g, L, gi);
-            I.j0 = segment_taps<NT>(S, ta, tb, I.L);
-            I.base = (l * g.R + r) * g.P + g.seg[gi].p0;
-            I.n = g.seg[gi].n;
-          }
-        }
+      if (P.r >= 0) {
+        I.j0 = segment_taps<NT>(g, P.r, gi, P.I, I.L);
+        I.base = (P.l * g.R + P.r) * g.P + g.seg[gi].p0;
+        I.n = g.seg[gi].n;
       }
       items[it] = I;
     }
     __syncthreads();
+    // 3. gather
     if (live && tz < nz) {
-      for (int it = 0; it < nv * per_view; ++it) {
+      for (int it = 0; it < nv * g.nr_max * g.n_seg; ++it) {
         const Item<NT> I = items[it];
         if (I.n == 0) continue;
         const int q = tz + I.j0;
@@ -394,10 +437,11 @@ static int fwd_threads(int P, int* ppt) {
 
 template <int NT, int PPT, int MODE>
 static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cudaStream_t s, int threads) {
-  int rpc = 64;
   auto bytes = [&](int rows) {
-    return (size_t)(2 * rows) * (sizeof(Entry) + (size_t)g.n_seg * sizeof(int) + (size_t)g.n_seg * NT * sizeof(float));
+    const size_t cap = (size_t)kCandPerRow * rows;
+    return cap * (sizeof(Entry) + (size_t)g.n_seg * sizeof(int) + (size_t)g.n_seg * NT * sizeof(float));
   };
+  int rpc = 64;
   while (rpc > 8 && bytes(rpc) > 40 * 1024) rpc /= 2;
   const size_t smem = bytes(rpc);
   if (smem > 48 * 1024) {
@@ -454,7 +498,7 @@ static cudaError_t bwd_launch(const DevGeom& g, int subset, const BwdArgs& a, cu
   if (vchunk < 1) vchunk = 1;
   const int nviews = subset_views(g, subset);
   if (vchunk > nviews) vchunk = nviews > 0 ? nviews : 1;
-  const size_t smem = (size_t)cpb * vchunk * per_view * sizeof(Item<NT>);
+  const size_t smem = (size_t)cpb * vchunk * g.nr_max * (sizeof(PixItem) + (size_t)g.n_seg * sizeof(Item<NT>));
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_backward<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
