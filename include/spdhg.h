@@ -173,6 +173,19 @@ int spdhg_sample(uint64_t seed, uint64_t offset, int n, const double* probs, int
 int spdhg_run(spdhg_ctx* ctx, const spdhg_params* params, float* x_inout, int where,
               spdhg_report* report, void* stream);
 
+/* The paper has no counterpart of this call.  y = P_i^T y for one subset (0 <= i < n_subsets),
+ * like spdhg_backproject, but the call allocates no device memory: for callers that cannot let
+ * a library call cudaMalloc (device memory owned by their own pool with a hard budget, or loops
+ * where an allocation's device synchronisation is not acceptable).  Its scratch is a fixed
+ * device array of 2^21 floats (8 MiB) inside the library, held by every device that loads the
+ * library until the process exits; a subset with more bins is rejected with SPDHG_ERR_ARG.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls share the array and
+ * every call overwrites the part it reads, so nothing has to be cleared between calls, but calls
+ * whose work overlaps on the GPU (concurrent streams, several contexts) race on it.  x and y are
+ * device pointers as in spdhg_backproject. */
+int spdhg_backproject_noalloc(spdhg_ctx* ctx, const float* y, float* x, int subset, void* stream);
+
 /* Kernel classes timed by the per-launch profiler. */
 enum { SPDHG_KERNEL_FORWARD = 0,   /* subset projection fused with the KL dual prox */
        SPDHG_KERNEL_BACKWARD = 1,  /* subset backprojection fused with z and the primal step */
