@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="set up the workload, run one data and one prior iteration, exit (ncu captures)")
     return ap.parse_args()
 
 
@@ -361,8 +363,34 @@ def run_ours(args):
     return 0
 
 
+def run_ncu_case():
+    """Few launches on the full workload: setup (252 sensitivity backprojections), then one data
+    iteration (k_forward, k_backward) and one dTV prior iteration (k_prior)."""
+    import torch
+
+    import paper_1808_07150_gb300 as pkg
+    from paper_1808_07150_gb300 import _build_ext
+    torch.cuda.set_device(0)
+    _build_ext.build()
+    sc, d = make_workload()
+    dev = torch.device("cuda", 0)
+
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a, np.float32).ravel()).to(dev)
+
+    with pkg.Context(sc) as ctx:
+        ctx.spdhg_set_data(to_dev(d["b"]), to_dev(d["r"]), to_dev(d["mult"]), to_dev(d["side"]))
+        ctx.spdhg_setup(pkg.make_params("dtv", alpha=ALPHA, dtv_gamma=0.995, dtv_eta_frac=0.01, seed=SEED))
+        ctx.spdhg_iterate([5, sc.n_subsets])
+        torch.cuda.synchronize()
+    print("ncu case done")
+    return 0
+
+
 def main():
     args = parse()
+    if args.ncu_case:
+        return run_ncu_case()
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
