@@ -126,20 +126,18 @@ class ClockSampler:
 
 
 def traffic_from_profiles(kernel_key):
-    """DRAM bytes per launch of `kernel_key` from a committed ncu summary, if its source matches."""
+    """DRAM bytes per launch of `kernel_key` from a committed ncu summary, provided the source
+    file named there is unchanged since the capture (else None)."""
     import hashlib
     src = os.path.join(ROOT, "paper_1808_07150_gb300", "csrc")
-    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         txt = open(path).read()
         m = re.search(rf"^traffic\[{re.escape(kernel_key)}\]:\s*([0-9.eE+]+)\s+bytes per launch\s+"
-                      rf"source_sha256\[(\w+)\]:\s*(\w+)", txt, re.M)
+                      rf"source_sha256\[([\w.]+)\]:\s*(\w+)", txt, re.M)
         if not m:
             continue
-        fname = {"prior": "prior.cu", "forward": "projector.cu", "backward": "projector.cu"}.get(kernel_key)
-        if fname is None:
-            continue
-        h = hashlib.sha256(open(os.path.join(src, fname), "rb").read()).hexdigest()[:16]
-        if h == m.group(3):
+        f = os.path.join(src, m.group(2))
+        if os.path.exists(f) and hashlib.sha256(open(f, "rb").read()).hexdigest()[:16] == m.group(3):
             return float(m.group(1))
     return None
 
