@@ -186,6 +186,18 @@ int spdhg_run(spdhg_ctx* ctx, const spdhg_params* params, float* x_inout, int wh
  * device pointers as in spdhg_backproject. */
 int spdhg_backproject_noalloc(spdhg_ctx* ctx, const float* y, float* x, int subset, void* stream);
 
+/* Launch-shape knobs of the iteration kernels (0 restores the built-in choice).  They change
+ * only how work is split across threads and blocks, never the arithmetic. */
+enum { SPDHG_TUNE_PRIOR_COLS = 0,   /* prior kernel: voxel columns per block, incl. one halo column */
+       SPDHG_TUNE_PRIOR_YCHUNK = 1, /* prior kernel: rows marched per block */
+       SPDHG_TUNE_FWD_SPLIT = 2,    /* forward kernel: blocks sharing the planes of one LOR line */
+       SPDHG_TUNE_BWD_COLS = 3,     /* backward kernel: voxel columns per block */
+       SPDHG_TUNE_KNOBS = 8 };
+
+/* Sets one launch-shape knob of the context (value 0: default).  Out-of-range values are rejected
+ * with SPDHG_ERR_ARG. */
+int spdhg_tune(spdhg_ctx* ctx, int knob, int value);
+
 /* Kernel classes timed by the per-launch profiler. */
 enum { SPDHG_KERNEL_FORWARD = 0,   /* subset projection fused with the KL dual prox */
        SPDHG_KERNEL_BACKWARD = 1,  /* subset backprojection fused with z and the primal step */

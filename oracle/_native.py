@@ -63,6 +63,7 @@ def lib():
         L.og_project_bins.argtypes = [gp, dp, ctypes.c_long, lp, dp]
         L.og_backproject_voxels.argtypes = [gp, dp, ctypes.c_int, ctypes.c_long, lp, dp]
         L.og_dense_clip.argtypes = [gp, dp]
+        L.og_subset_sums_at_voxels.argtypes = [gp, dp, ctypes.c_long, lp, dp]
         L.og_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -124,6 +125,15 @@ def adjoint_at_voxels(sc, y, voxels, subset=-1):
     voxels = np.ascontiguousarray(voxels, np.int64)
     out = np.zeros(len(voxels), np.float64)
     lib().og_backproject_voxels(CGeom(sc).ref, _dptr(y), int(subset), len(voxels), _lptr(voxels), _dptr(out))
+    return out
+
+
+def subset_adjoints_at_voxels(sc, w, voxels):
+    """(len(voxels), n_subsets): (L_i^T w) at each voxel for every subset i, by the definition."""
+    w = np.ascontiguousarray(w, np.float64)
+    voxels = np.ascontiguousarray(voxels, np.int64)
+    out = np.zeros((len(voxels), sc.n_subsets), np.float64)
+    lib().og_subset_sums_at_voxels(CGeom(sc).ref, _dptr(w), len(voxels), _lptr(voxels), _dptr(out))
     return out
 
 

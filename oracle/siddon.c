@@ -293,3 +293,26 @@ void og_dense_clip(const og_geom* g, double* A) {
               A[j * N + ((long)iy * g->nx + ix) * g->nz + iz] = og_clip_len(g, o, d, h, ix, iy, iz);
       }
 }
+
+/* out[k * n_subsets + i] = (L_i^T w)_{voxels[k]} for every subset i, by the definition (slab-
+ * clipped length of every LOR inside the voxel), in one pass over the bins. */
+void og_subset_sums_at_voxels(const og_geom* g, const double* w, long n, const long* voxels, double* out) {
+  const int R = g->n_radial, P = og_n_planes(g), V = g->n_views, m = g->n_subsets;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long k = 0; k < n; ++k) {
+    long vox = voxels[k];
+    int iz = (int)(vox % g->nz);
+    int ix = (int)((vox / g->nz) % g->nx);
+    int iy = (int)(vox / ((long)g->nz * g->nx));
+    for (int i = 0; i < m; ++i) out[k * m + i] = 0.0;
+    for (int v = 0; v < V; ++v)
+      for (int r = 0; r < R; ++r)
+        for (int p = 0; p < P; ++p) {
+          long j = ((long)v * R + r) * P + p;
+          double o[3], d[3], h;
+          og_lor(g, v, r, p, o, d, &h);
+          double l = og_clip_len(g, o, d, h, ix, iy, iz);
+          if (l != 0.0) out[k * m + (v % m)] += l * w[j];
+        }
+  }
+}

@@ -151,6 +151,11 @@ class Context:
                     epoch_ms=ms[:params.epochs])
 
 
+    def spdhg_tune(self, knob, value):
+        """Sets a launch-shape knob ('prior_cols', 'prior_ychunk', 'fwd_split', 'bwd_cols'); 0 = default."""
+        code = _capi.TUNE[knob] if isinstance(knob, str) else int(knob)
+        self._check(_capi.lib().spdhg_tune(self.h, code, int(value)))
+
     def spdhg_profile(self, enable=True):
         self._check(_capi.lib().spdhg_profile(self.h, int(bool(enable))))
 

@@ -24,8 +24,9 @@ _EXPORTS = [
     "spdhg_create", "spdhg_destroy", "spdhg_last_error", "spdhg_sizes", "spdhg_set_data",
     "spdhg_project", "spdhg_backproject", "spdhg_setup", "spdhg_iterate", "spdhg_get",
     "spdhg_objective", "spdhg_probabilities", "spdhg_sample", "spdhg_run", "spdhg_profile",
-    "spdhg_profile_read", "spdhg_backproject_noalloc",
+    "spdhg_profile_read", "spdhg_backproject_noalloc", "spdhg_tune",
 ]
+TUNE = {"prior_cols": 0, "prior_ychunk": 1, "fwd_split": 2, "bwd_cols": 3}
 KERNELS = ["forward", "backward", "prior", "tgv", "w_step"]
 
 
@@ -99,6 +100,7 @@ def lib():
             "spdhg_profile": ([vp, i32], i32),
             "spdhg_profile_read": ([vp, P(dp), P(i64), i32], i32),
             "spdhg_backproject_noalloc": ([vp, vp, vp, i32, vp], i32),
+            "spdhg_tune": ([vp, i32, i32], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)

@@ -765,6 +765,28 @@ done:
   return status;
 }
 
+int spdhg_tune(spdhg_ctx* ctx, int knob, int value) {
+  if (!ctx || knob < 0 || knob >= SPDHG_TUNE_KNOBS || value < 0) return SPDHG_ERR_ARG;
+  const int zw = (ctx->dg.nz + 31) / 32;
+  switch (knob) {
+    case SPDHG_TUNE_PRIOR_COLS:
+      if (value != 0 && (value < 2 || value * zw > 32)) return fail(ctx, SPDHG_ERR_ARG, "prior cols out of range");
+      break;
+    case SPDHG_TUNE_PRIOR_YCHUNK:
+      if (value > 1 << 20) return fail(ctx, SPDHG_ERR_ARG, "ychunk out of range");
+      break;
+    case SPDHG_TUNE_FWD_SPLIT:
+      if (value > 16) return fail(ctx, SPDHG_ERR_ARG, "forward split out of range");
+      break;
+    case SPDHG_TUNE_BWD_COLS:
+      if (value != 0 && (value & (value - 1))) return fail(ctx, SPDHG_ERR_ARG, "backward cols must be a power of two");
+      break;
+    default: break;
+  }
+  ctx->dg.tune[knob] = value;
+  return SPDHG_OK;
+}
+
 int spdhg_profile(spdhg_ctx* ctx, int enable) {
   if (!ctx) return SPDHG_ERR_ARG;
   for (auto& r : ctx->prof_pending) {

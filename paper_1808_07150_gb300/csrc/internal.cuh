@@ -40,6 +40,7 @@ struct DevGeom {
   const float4* rs;      // per (radial bin, segment): kappa_hi, kappa_lo, len_scale, 0
   const SegDev* seg;
   const int* plane_seg;  // plane -> segment
+  int tune[SPDHG_TUNE_KNOBS];  // launch-shape overrides (0: built-in heuristic)
 };
 
 // Views of subset i: i, i+m, ...  (subset < 0: all views).

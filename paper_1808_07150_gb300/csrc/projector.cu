@@ -182,28 +182,32 @@ __device__ __forceinline__ int row_entries(const DevGeom& g, const Line& L, bool
 }
 
 template <int NT, int PPT, int MODE>
-__global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc, FwdArgs a) {
+__global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc, int split, FwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int warp_tot[2];
   __shared__ int n_ent_sh;
   const int cap = kCandPerRow * rpc;
   Entry* ent = reinterpret_cast<Entry*>(smem);
-  int* tapJ = reinterpret_cast<int*>(ent + cap);
+  int* tapJ = reinterpret_cast<int*>(ent + cap);   // j0 | (nt << 24) per (segment, entry)
   float* tapL = reinterpret_cast<float*>(tapJ + g.n_seg * cap);
 
-  const int line = blockIdx.x;
+  // block = (line, part): `split` blocks share the planes of one LOR line
+  const int line = blockIdx.x / split, part = blockIdx.x - line * split;
   const int l = line / g.R, r = line - (line / g.R) * g.R;
   const int v = subset_view(g, subset, l);
   const Line L = make_line(g, v, r);
+  const int per_part = (g.P + split - 1) / split;
+  const int p_lo = part * per_part, p_hi = min(g.P, p_lo + per_part);
+  const int g_lo = g.plane_seg[min(p_lo, g.P - 1)], g_hi = g.plane_seg[max(p_hi - 1, 0)];
 
   int pseg[PPT], pq[PPT];
   float acc[PPT], chord[PPT];
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    const int p = threadIdx.x + k * blockDim.x;
+    const int p = p_lo + threadIdx.x + k * blockDim.x;
     acc[k] = 0.f;
     chord[k] = 0.f;
-    if (p < g.P) {
+    if (p < p_hi) {
       const int gi = g.plane_seg[p];
       pseg[k] = gi;
       pq[k] = p - g.seg[gi].p0;
@@ -215,6 +219,7 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc,
   const bool ydom = fabsf(L.c_hi) >= fabsf(L.s_hi);  // |dy| >= |dx|: walk the rows of y
   const int nrows = ydom ? g.ny : g.nx;
   const int nz = g.nz;
+  const int nseg_part = g_hi - g_lo + 1;
 
   for (int row0 = 0; row0 < nrows; row0 += rpc) {
     // 1. rows -> exact pixel intervals, compacted with a two-warp prefix sum (rpc <= 64)
@@ -240,13 +245,15 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc,
     }
     __syncthreads();
     const int n_ent = n_ent_sh;
-    // 2. axial taps of every (entry, segment)
-    for (int it = threadIdx.x; it < g.n_seg * n_ent; it += blockDim.x) {
-      const int gi = it / n_ent, e = it - gi * n_ent;
+    // 2. axial taps of every (entry, segment of this block's planes)
+    for (int it = threadIdx.x; it < nseg_part * n_ent; it += blockDim.x) {
+      const int gi = g_lo + it / n_ent, e = it - (it / n_ent) * n_ent;
       float Lk[NT];
       const int j0 = segment_taps<NT>(g, r, gi, ent[e].I, Lk);
+      int nt = NT;
+      while (nt > 1 && Lk[nt - 1] == 0.f) --nt;
       const int slot = gi * cap + e;
-      tapJ[slot] = j0;
+      tapJ[slot] = (j0 & 0xffffff) | (nt << 24);
 #pragma unroll
       for (int k = 0; k < NT; ++k) tapL[slot * NT + k] = Lk[k];
     }
@@ -258,14 +265,18 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc,
       for (int k = 0; k < PPT; ++k) {
         if (pseg[k] < 0) continue;
         const int slot = pseg[k] * cap + e;
-        const int iz = pq[k] - tapJ[slot];
+        const int jn = tapJ[slot];
+        const int nt = jn >> 24;
+        const int iz = pq[k] - ((jn << 8) >> 8);  // sign-extended j0
 #pragma unroll
         for (int t = 0; t < NT; ++t) {
-          const float Lt = tapL[slot * NT + t];
-          const int izt = iz - t;
-          if (izt >= 0 && izt < nz) {
-            acc[k] = fmaf(Lt, __ldg(xc + izt), acc[k]);
-            if (MODE != FWD_PROJECT) chord[k] += Lt;
+          if (t < nt) {
+            const float Lt = tapL[slot * NT + t];
+            const int izt = iz - t;
+            if ((unsigned)izt < (unsigned)nz) {
+              acc[k] = fmaf(Lt, __ldg(xc + izt), acc[k]);
+              if (MODE != FWD_PROJECT) chord[k] += Lt;
+            }
           }
         }
       }
@@ -275,8 +286,8 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc,
 
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    const int p = threadIdx.x + k * blockDim.x;
-    if (p >= g.P) continue;
+    const int p = p_lo + threadIdx.x + k * blockDim.x;
+    if (p >= p_hi) continue;
     const size_t j = ((size_t)v * g.R + r) * g.P + p;
     const float mu = a.mult ? a.mult[j] : 1.f;
     if (MODE == FWD_PROJECT) {
@@ -310,25 +321,31 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc,
 template <int NT>
 struct Item {
   int base;  // subset-local sinogram index of (view, radial, first plane of the segment)
-  int n;     // planes in the segment (0: no contribution)
+  int n;     // planes in the segment
   int j0;
+  int nt;    // taps actually used (trailing zero-length taps dropped)
   float L[NT];
 };
 
 struct PixItem {
-  int l, r;  // view (subset-local) and radial bin; r < 0: no intersection
+  int l, r;  // view (subset-local) and radial bin
   PixInt I;
 };
+
+// Candidate (view, bin) pairs of the pixel footprint handled per chunk by the first warp of a
+// column; the pairs that intersect the pixel are compacted with a warp ballot.
+constexpr int kPairsPerChunk = 32;
 
 template <int NT, int MODE>
 __global__ void __launch_bounds__(256) k_backward(DevGeom g, int subset, int tpc, int cpb, int vchunk,
                                                   BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int n_pix = vchunk * g.nr_max;
-  const int items_per_col = n_pix * g.n_seg;
+  __shared__ int n_pairs_sh[8];
+  const int items_per_col = kPairsPerChunk * g.n_seg;
   const int cb = threadIdx.x / tpc;
-  PixItem* pix = reinterpret_cast<PixItem*>(smem) + cb * n_pix;
-  Item<NT>* items = reinterpret_cast<Item<NT>*>(reinterpret_cast<PixItem*>(smem) + cpb * n_pix) + cb * items_per_col;
+  PixItem* pix = reinterpret_cast<PixItem*>(smem) + cb * kPairsPerChunk;
+  Item<NT>* items = reinterpret_cast<Item<NT>*>(reinterpret_cast<PixItem*>(smem) + cpb * kPairsPerChunk) +
+                    cb * items_per_col;
   const int tz = threadIdx.x % tpc;
   const int col = blockIdx.x * cpb + cb;
   const bool live = col < g.nx * g.ny;
@@ -341,13 +358,12 @@ __global__ void __launch_bounds__(256) k_backward(DevGeom g, int subset, int tpc
 
   for (int l0 = 0; l0 < nviews; l0 += vchunk) {
     const int nv = min(vchunk, nviews - l0);
-    // 1. (view, radial bin) pairs of the pixel footprint -> exact pixel intervals
-    for (int it = tz; it < nv * g.nr_max; it += tpc) {
-      const int l = l0 + it / g.nr_max, ri = it % g.nr_max;
+    // 1. footprint pairs -> exact pixel intervals, compacted (first warp of the column)
+    if (tz < 32) {
       PixItem P;
-      P.l = l;
-      P.r = -1;
-      if (live) {
+      bool ok = false;
+      if (live && tz < nv * g.nr_max) {
+        const int l = l0 + tz / g.nr_max, ri = tz % g.nr_max;
         const int v = subset_view(g, subset, l);
         const float4 cs = g.view[v];
         const float sc = Xc * cs.x + Yc * cs.z;
@@ -357,40 +373,44 @@ __global__ void __launch_bounds__(256) k_backward(DevGeom g, int subset, int tpc
         const int r = rlo + ri;
         if (r >= 0 && r < g.R && r <= rhi) {
           const Line L = make_line(g, v, r);
-          if (pixel_interval(g, L, ix, iy, P.I)) P.r = r;
+          ok = pixel_interval(g, L, ix, iy, P.I);
+          P.l = l;
+          P.r = r;
         }
       }
-      pix[it] = P;
+      const unsigned mask = __ballot_sync(0xffffffffu, ok);
+      if (ok) pix[__popc(mask & ((1u << tz) - 1u))] = P;
+      if (tz == 0) n_pairs_sh[cb] = __popc(mask);
     }
     __syncthreads();
+    const int np = n_pairs_sh[cb];
     // 2. axial taps per (pair, segment)
-    for (int it = tz; it < nv * g.nr_max * g.n_seg; it += tpc) {
+    for (int it = tz; it < np * g.n_seg; it += tpc) {
       const int pi = it / g.n_seg, gi = it - pi * g.n_seg;
       const PixItem P = pix[pi];
       Item<NT> I;
-      I.n = 0;
-      I.base = 0;
-      I.j0 = 0;
-#pragma unroll
-      for (int k = 0; k < NT; ++k) I.L[k] = 0.f;
-      if (P.r >= 0) {
-        I.j0 = segment_taps<NT>(g, P.r, gi, P.I, I.L);
-        I.base = (P.l * g.R + P.r) * g.P + g.seg[gi].p0;
-        I.n = g.seg[gi].n;
-      }
+      I.j0 = segment_taps<NT>(g, P.r, gi, P.I, I.L);
+      I.base = (P.l * g.R + P.r) * g.P + g.seg[gi].p0;
+      I.n = g.seg[gi].n;
+      int nt = NT;
+      while (nt > 1 && I.L[nt - 1] == 0.f) --nt;
+      I.nt = nt;
       items[it] = I;
     }
     __syncthreads();
-    // 3. gather
+    // 3. gather along contiguous plane runs
     if (live && tz < nz) {
-      for (int it = 0; it < nv * g.nr_max * g.n_seg; ++it) {
+      const int ni = np * g.n_seg;
+      for (int it = 0; it < ni; ++it) {
         const Item<NT> I = items[it];
-        if (I.n == 0) continue;
         const int q = tz + I.j0;
+        const float* __restrict__ wp = a.w + I.base;
 #pragma unroll
         for (int k = 0; k < NT; ++k) {
-          const int qk = q + k;
-          if (qk >= 0 && qk < I.n) acc = fmaf(I.L[k], __ldg(a.w + I.base + qk), acc);
+          if (k < I.nt) {
+            const int qk = q + k;
+            if ((unsigned)qk < (unsigned)I.n) acc = fmaf(I.L[k], __ldg(wp + qk), acc);
+          }
         }
       }
     }
@@ -426,17 +446,22 @@ __global__ void k_gather_subset(DevGeom g, int subset, const float* __restrict__
 // launchers
 // ---------------------------------------------------------------------------------------
 
-static int fwd_threads(int P, int* ppt) {
-  int t = (P + 2) / 3;
+static int fwd_split(const DevGeom& g) {
+  if (g.tune[SPDHG_TUNE_FWD_SPLIT]) return g.tune[SPDHG_TUNE_FWD_SPLIT];
+  return g.P >= 512 ? 4 : (g.P >= 256 ? 2 : 1);  // enough blocks per SM for long plane lists
+}
+
+static int fwd_threads(int planes, int* ppt) {
+  int t = (planes + 2) / 3;
   t = ((t + 31) / 32) * 32;
   t = t < 128 ? 128 : (t > 512 ? 512 : t);
-  int k = (P + t - 1) / t;
+  int k = (planes + t - 1) / t;
   *ppt = k < 1 ? 1 : k;
   return t;
 }
 
 template <int NT, int PPT, int MODE>
-static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cudaStream_t s, int threads) {
+static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cudaStream_t s, int threads, int split) {
   auto bytes = [&](int rows) {
     const size_t cap = (size_t)kCandPerRow * rows;
     return cap * (sizeof(Entry) + (size_t)g.n_seg * sizeof(int) + (size_t)g.n_seg * NT * sizeof(float));
@@ -450,19 +475,21 @@ static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cu
   }
   const int lines = subset_views(g, subset) * g.R;
   if (lines == 0) return cudaSuccess;
-  k_forward<NT, PPT, MODE><<<lines, threads, smem, s>>>(g, subset, rpc, a);
+  k_forward<NT, PPT, MODE><<<lines * split, threads, smem, s>>>(g, subset, rpc, split, a);
   return cudaGetLastError();
 }
 
 template <int NT, int MODE>
 static cudaError_t fwd_ppt(const DevGeom& g, int subset, const FwdArgs& a, cudaStream_t s) {
+  int split = fwd_split(g);
+  if (split > g.P) split = g.P;
   int ppt;
-  const int threads = fwd_threads(g.P, &ppt);
+  const int threads = fwd_threads((g.P + split - 1) / split, &ppt);
   switch (ppt) {
-    case 1: return fwd_launch<NT, 1, MODE>(g, subset, a, s, threads);
-    case 2: return fwd_launch<NT, 2, MODE>(g, subset, a, s, threads);
-    case 3: return fwd_launch<NT, 3, MODE>(g, subset, a, s, threads);
-    case 4: return fwd_launch<NT, 4, MODE>(g, subset, a, s, threads);
+    case 1: return fwd_launch<NT, 1, MODE>(g, subset, a, s, threads, split);
+    case 2: return fwd_launch<NT, 2, MODE>(g, subset, a, s, threads, split);
+    case 3: return fwd_launch<NT, 3, MODE>(g, subset, a, s, threads, split);
+    case 4: return fwd_launch<NT, 4, MODE>(g, subset, a, s, threads, split);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -491,14 +518,13 @@ template <int NT, int MODE>
 static cudaError_t bwd_launch(const DevGeom& g, int subset, const BwdArgs& a, cudaStream_t s) {
   int tpc = ((g.nz + 31) / 32) * 32;
   if (tpc > 256) return cudaErrorInvalidValue;
-  const int cpb = 256 / tpc;
-  const int per_view = g.nr_max * g.n_seg;
-  const int budget = 160;  // items per column and chunk
-  int vchunk = budget / per_view;
-  if (vchunk < 1) vchunk = 1;
+  int cpb = tpc >= 128 ? 1 : 256 / tpc;
+  if (g.tune[SPDHG_TUNE_BWD_COLS] && g.tune[SPDHG_TUNE_BWD_COLS] * tpc <= 256) cpb = g.tune[SPDHG_TUNE_BWD_COLS];
+  int vchunk = kPairsPerChunk / g.nr_max;  // views whose footprint pairs fit one warp
+  if (vchunk < 1) return cudaErrorInvalidValue;
   const int nviews = subset_views(g, subset);
   if (vchunk > nviews) vchunk = nviews > 0 ? nviews : 1;
-  const size_t smem = (size_t)cpb * vchunk * g.nr_max * (sizeof(PixItem) + (size_t)g.n_seg * sizeof(Item<NT>));
+  const size_t smem = (size_t)cpb * kPairsPerChunk * (sizeof(PixItem) + (size_t)g.n_seg * sizeof(Item<NT>));
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_backward<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

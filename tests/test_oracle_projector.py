@@ -134,3 +134,13 @@ def test_project_bins_matches_full_projection():
     full = _native.line_integrals(sc, x).ravel()
     bins = np.arange(0, sc.n_bins, 7, dtype=np.int64)
     np.testing.assert_array_equal(_native.line_integrals_at(sc, x, bins), full[bins])
+
+
+def test_subset_adjoints_at_voxels_match_per_subset_backprojection():
+    sc = synth.tiny_3d(n_subsets=2, steep=True)
+    w = synth.random_sinogram(sc, 6).astype(np.float64)
+    vox = np.arange(0, sc.n_voxels, 7, dtype=np.int64)
+    got = _native.subset_adjoints_at_voxels(sc, w, vox)
+    for i in range(sc.n_subsets):
+        ref = oracle.backproject(sc, w * oracle.subset_mask(sc, i), i).ravel()[vox]
+        np.testing.assert_allclose(got[:, i], ref, rtol=1e-12, atol=1e-12)
