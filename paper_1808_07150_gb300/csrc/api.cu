@@ -179,6 +179,9 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
     kappa_max = std::max(kappa_max, fabs(g.seg_dz[k]) / (2.0 * hmin * g.vz));
   }
   if (P > 512 * kMaxPlanesPerThread) return SPDHG_ERR_UNSUPPORTED;
+  // kernels index images (up to 6 components) and sinograms with 32-bit integers
+  if ((double)g.nx * g.ny * g.nz * 6 >= 2147483647.0 || (double)g.n_views * g.n_radial * P >= 2147483647.0)
+    return SPDHG_ERR_UNSUPPORTED;
   const double dt_max = sqrt(2.0) * g.vx;  // longest transaxial chord of a pixel
   const int taps = kappa_max == 0.0 ? 1 : (int)ceil(1.0 + kappa_max * dt_max * (1.0 + 1e-6));
   if (taps > kMaxTaps) return SPDHG_ERR_UNSUPPORTED;
@@ -770,7 +773,7 @@ int spdhg_tune(spdhg_ctx* ctx, int knob, int value) {
   const int zw = (ctx->dg.nz + 31) / 32;
   switch (knob) {
     case SPDHG_TUNE_PRIOR_COLS:
-      if (value != 0 && (value < 2 || value * zw > 32)) return fail(ctx, SPDHG_ERR_ARG, "prior cols out of range");
+      if (value != 0 && (value < 2 || value * zw > 16)) return fail(ctx, SPDHG_ERR_ARG, "prior cols out of range");
       break;
     case SPDHG_TUNE_PRIOR_YCHUNK:
       if (value > 1 << 20) return fail(ctx, SPDHG_ERR_ARG, "ychunk out of range");

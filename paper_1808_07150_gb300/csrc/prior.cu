@@ -13,14 +13,15 @@ namespace spdhg {
 
 // Dual update of one voxel: g = A_n x (forward differences; dTV: D g with
 // D = I - gamma_d xi xi^T, xi = grad v / sqrt(|grad v|^2 + eta^2)), q+ = proj(q + sigma g),
-// b = D^T (q+ - q).  Returns b and q+.
+// b = D^T (q+ - q).  The ball projection q+ = qa min(1, alpha / |qa|) uses one reciprocal
+// square root.  Returns b and q+.
 template <int KIND>
 __device__ __forceinline__ void dual_update(const PriorArgs& a, const float gr_in[3], const float gv[3],
                                             const float qo[3], float b[3], float qn[3]) {
   float gr[3] = {gr_in[0], gr_in[1], gr_in[2]};
   float xi[3] = {0.f, 0.f, 0.f};
   if (KIND == SPDHG_PRIOR_DTV) {
-    const float inv = __frsqrt_rn(fmaf(gv[0], gv[0], fmaf(gv[1], gv[1], fmaf(gv[2], gv[2], a.eta2))));
+    const float inv = rsqrtf(fmaf(gv[0], gv[0], fmaf(gv[1], gv[1], fmaf(gv[2], gv[2], a.eta2))));
 #pragma unroll
     for (int k = 0; k < 3; ++k) xi[k] = gv[k] * inv;
     const float gd = a.gamma_d * (xi[0] * gr[0] + xi[1] * gr[1] + xi[2] * gr[2]);
@@ -34,10 +35,10 @@ __device__ __forceinline__ void dual_update(const PriorArgs& a, const float gr_i
 #pragma unroll
     for (int k = 0; k < 3; ++k) qn[k] = fminf(fmaxf(qa[k], -a.alpha), a.alpha);
   } else {
-    const float nrm = sqrtf(qa[0] * qa[0] + qa[1] * qa[1] + qa[2] * qa[2]);
-    const float sc = fmaxf(1.f, nrm / a.alpha);
+    const float n2 = fmaf(qa[0], qa[0], fmaf(qa[1], qa[1], qa[2] * qa[2]));
+    const float sc = fminf(1.f, a.alpha * rsqrtf(n2));  // n2 = 0 gives +inf -> 1
 #pragma unroll
-    for (int k = 0; k < 3; ++k) qn[k] = qa[k] / sc;
+    for (int k = 0; k < 3; ++k) qn[k] = qa[k] * sc;
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) b[k] = qn[k] - qo[k];
@@ -48,127 +49,128 @@ __device__ __forceinline__ void dual_update(const PriorArgs& a, const float gr_i
   }
 }
 
-// One block owns `cols - 1` voxel columns in x (plus one halo column on the lower side whose
-// duals are recomputed, not written) and the whole z extent (warps along z, so every access is
-// a contiguous 128-byte line), and marches along y over `ychunk` rows (plus one warm-up row).
-// The dual change of the lower y neighbour is carried in registers, the lower x neighbour's in
-// shared memory and the lower z neighbour's by a warp shuffle, so each voxel's dual is computed
-// once (plus the halo) and every array is streamed once.
-// Operands of one voxel row step, loaded one row ahead (software pipelining): the loads of
-// row iy + 1 are in flight while row iy is computed.
-struct RowLoads {
-  float xz, xx, vz, vx, q0, q1, q2, zv, tv;
-};
-
-template <int KIND>
-__device__ __forceinline__ void load_row(const PriorArgs& a, int64_t idx, int64_t N, int sx, bool hx, bool hz,
-                                         bool owner, float xc, float vc, RowLoads& L) {
-  L.xz = hz ? __ldg(a.x_in + idx + 1) : xc;
-  L.xx = hx ? __ldg(a.x_in + idx + sx) : xc;
-  if (KIND == SPDHG_PRIOR_DTV) {
-    L.vz = hz ? __ldg(a.side + idx + 1) : vc;
-    L.vx = hx ? __ldg(a.side + idx + sx) : vc;
-  } else {
-    L.vz = L.vx = 0.f;
-  }
-  L.q0 = __ldg(a.q_in + idx);
-  L.q1 = __ldg(a.q_in + N + idx);
-  L.q2 = __ldg(a.q_in + 2 * N + idx);
-  L.zv = owner ? a.z[idx] : 0.f;  // z and T only matter where the block writes
-  L.tv = owner ? __ldg(a.T + idx) : 0.f;
+// 4-byte asynchronous global -> shared copy; src_bytes = 0 fills the destination with zero.
+// `base` is a valid address of the same array, used as the (unread) source when !valid.
+__device__ __forceinline__ void cp_async4(float* dst, const float* base, int off, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const float* src = valid ? base + off : base;
+  const int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+constexpr int kPriorStages = 4;  // rows resident or in flight: iy, iy+1 (used), iy+2, iy+3 (loading)
 
 // One block owns `cols - 1` voxel columns in x (plus one halo column on the lower side whose
 // duals are recomputed, not written) and the whole z extent (warps along z, so every access is
 // a contiguous 128-byte line), and marches along y over `ychunk` rows (plus one warm-up row).
-// The dual change of the lower y neighbour is carried in registers, the lower x neighbour's in
-// shared memory and the lower z neighbour's by a warp shuffle, so each voxel's dual is computed
-// once (plus the halo) and every array is streamed once.  Loads run one row (x, v: two rows)
-// ahead of the arithmetic.
+// Rows are staged in shared memory by a 4-stage cp.async pipeline: each thread copies its own
+// voxel's operands (x, v also for one upper halo column), neighbours are read from the staged
+// rows, the lower y neighbour's dual change is carried in a register and the lower x / z
+// neighbours' through shared memory.  Every array is read from HBM once per row.
 template <int KIND>
-__global__ void __launch_bounds__(1024) k_prior(DevGeom g, PriorArgs a, int cols, int ychunk) {
+__global__ void __launch_bounds__(512) k_prior(DevGeom g, PriorArgs a, int cols, int ychunk) {
   extern __shared__ float sh[];
-  const int zw = (g.nz + 31) >> 5;           // warps per column
-  float* sbx = sh;                            // [cols][zw * 32]: b_x of the current row
-  float* sbz = sh + cols * zw * 32;           // [cols][zw]: b_z of lane 31 of each z-warp
+  const int zw = (g.nz + 31) >> 5;
+  const int zc = zw * 32;                     // staged z extent
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int c = w / zw, zi = w - c * zw;
-  const int ix = blockIdx.x * (cols - 1) + c - 1;
   const int iz = zi * 32 + lane;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int64_t N = (int64_t)nx * ny * nz;
-  const int sx = nz;
-  const int64_t sy = (int64_t)nx * nz;
+  const int N = nx * ny * nz;
+  const int sy = nx * nz;
+  const int x0 = blockIdx.x * (cols - 1) - 1;  // x of column 0 (the lower halo)
+  const int ix = x0 + c;
   const bool live = ix >= 0 && ix < nx && iz < nz;
   const bool owner = live && c >= 1;
   const int y0 = blockIdx.y * ychunk, y1 = min(ny, y0 + ychunk);
+  const int ys = y0 > 0 ? y0 - 1 : 0;         // first row computed (warm-up row for y0 > 0)
+  const int ylast = min(y1, ny - 1);          // last row whose x / v are needed
   const bool hx = ix < nx - 1, hz = iz < nz - 1;
+  const bool dtv = KIND == SPDHG_PRIOR_DTV;
 
-  int iy = y0 > 0 ? y0 - 1 : 0;
-  int64_t idx = live ? ((int64_t)iy * nx + ix) * nz + iz : 0;
-  float xc = 0.f, vc = 0.f, xn = 0.f, vn = 0.f;
-  RowLoads cur{};
-  if (live) {
-    xc = __ldg(a.x_in + idx);
-    if (KIND == SPDHG_PRIOR_DTV) vc = __ldg(a.side + idx);
-    const bool hy = iy < ny - 1;
-    xn = hy ? __ldg(a.x_in + idx + sy) : xc;
-    if (KIND == SPDHG_PRIOR_DTV) vn = hy ? __ldg(a.side + idx + sy) : vc;
-    load_row<KIND>(a, idx, N, sx, hx, hz, owner, xc, vc, cur);
+  // stage layout: x, v: (cols + 1) x zc; q0, q1, q2, z, T: cols x zc
+  const int xv_sz = (cols + 1) * zc, cell_sz = cols * zc;
+  const int stage_sz = 2 * xv_sz + 5 * cell_sz;
+  float* sbx = sh + kPriorStages * stage_sz;  // [cols][zc] b_x of the current row
+  float* sbz = sbx + cell_sz;                 // [cols][zc] b_z of the current row
+  const int me = c * zc + iz;
+
+  auto issue_row = [&](int row) {
+    float* st = sh + (row % kPriorStages) * stage_sz;
+    const int base = row * sy + ix * nz + iz;  // only dereferenced when valid
+    cp_async4(st + me, a.x_in, base, live);
+    if (dtv) cp_async4(st + xv_sz + me, a.side, base, live);
+    cp_async4(st + 2 * xv_sz + me, a.q_in, base, live);
+    cp_async4(st + 2 * xv_sz + cell_sz + me, a.q_in, N + base, live);
+    cp_async4(st + 2 * xv_sz + 2 * cell_sz + me, a.q_in, 2 * N + base, live);
+    cp_async4(st + 2 * xv_sz + 3 * cell_sz + me, a.z, base, owner);
+    cp_async4(st + 2 * xv_sz + 4 * cell_sz + me, a.T, base, owner);
+    if (c == 0) {  // upper halo column: x and v of x0 + cols
+      const int ixh = x0 + cols;
+      const bool vh = ixh < nx && iz < nz;
+      const int bh = row * sy + ixh * nz + iz;
+      cp_async4(st + cols * zc + iz, a.x_in, bh, vh);
+      if (dtv) cp_async4(st + xv_sz + cols * zc + iz, a.side, bh, vh);
+    }
+  };
+
+  for (int k = 0; k < kPriorStages - 1; ++k) {
+    if (ys + k <= ylast) issue_row(ys + k);
+    cp_async_commit();
   }
   float by_prev = 0.f;
-  for (; iy < y1; ++iy, idx += sy) {
+  for (int iy = ys; iy < y1; ++iy) {
+    if (iy + kPriorStages - 1 <= ylast) issue_row(iy + kPriorStages - 1);
+    cp_async_commit();
+    cp_async_wait<kPriorStages - 2>();  // rows iy and iy + 1 have landed
+    __syncthreads();
+    const float* st = sh + (iy % kPriorStages) * stage_sz;
+    const float* sn = sh + ((iy + 1) % kPriorStages) * stage_sz;
     const bool hy = iy < ny - 1;
-    // prefetch: operands of row iy + 1, and x, v of row iy + 2
-    RowLoads nxt = cur;
-    float xnn = xn, vnn = vn;
-    const bool more = live && iy + 1 < y1;
-    if (more) {
-      load_row<KIND>(a, idx + sy, N, sx, hx, hz, owner, xn, vn, nxt);
-      const bool hy1 = iy + 1 < ny - 1;
-      xnn = hy1 ? __ldg(a.x_in + idx + 2 * sy) : xn;
-      if (KIND == SPDHG_PRIOR_DTV) vnn = hy1 ? __ldg(a.side + idx + 2 * sy) : vn;
-    }
     float b[3] = {0.f, 0.f, 0.f}, qn[3] = {0.f, 0.f, 0.f};
+    const float xc = st[me];
     if (live) {
-      const float gr[3] = {cur.xx - xc, hy ? xn - xc : 0.f, cur.xz - xc};
+      const float gr[3] = {hx ? st[me + zc] - xc : 0.f, hy ? sn[me] - xc : 0.f, hz ? st[me + 1] - xc : 0.f};
       float gv[3] = {0.f, 0.f, 0.f};
-      if (KIND == SPDHG_PRIOR_DTV) {
-        gv[0] = cur.vx - vc;
-        gv[1] = hy ? vn - vc : 0.f;
-        gv[2] = cur.vz - vc;
+      if (dtv) {
+        const float* sv = st + xv_sz;
+        const float vc = sv[me];
+        gv[0] = hx ? sv[me + zc] - vc : 0.f;
+        gv[1] = hy ? sn[xv_sz + me] - vc : 0.f;
+        gv[2] = hz ? sv[me + 1] - vc : 0.f;
       }
-      const float qo[3] = {cur.q0, cur.q1, cur.q2};
+      const float* sq = st + 2 * xv_sz;
+      const float qo[3] = {sq[me], sq[cell_sz + me], sq[2 * cell_sz + me]};
       dual_update<KIND>(a, gr, gv, qo, b, qn);
     }
-    const float bz_lo = __shfl_up_sync(0xffffffffu, b[2], 1);
-    sbx[c * zw * 32 + zi * 32 + lane] = b[0];
-    if (lane == 31) sbz[c * zw + zi] = b[2];
+    sbx[me] = b[0];
+    sbz[me] = b[2];
     __syncthreads();
     if (owner && iy >= y0) {
+      const int idx = iy * sy + ix * nz + iz;
       a.q_out[idx] = qn[0];
       a.q_out[N + idx] = qn[1];
       a.q_out[2 * N + idx] = qn[2];
       // dz = A_n^T dq = sum_a [k_a >= 1] b_a(k - e_a) - [k_a < n_a - 1] b_a(k)
       float dz = 0.f;
-      if (ix > 0) dz += sbx[(c - 1) * zw * 32 + zi * 32 + lane];
+      if (ix > 0) dz += sbx[me - zc];
       if (iy > 0) dz += by_prev;
-      if (iz > 0) dz += lane > 0 ? bz_lo : sbz[c * zw + zi - 1];
+      if (iz > 0) dz += sbz[me - 1];
       if (hx) dz -= b[0];
       if (hy) dz -= b[1];
       if (hz) dz -= b[2];
-      const float zn = cur.zv + dz;
+      const float* sq = st + 2 * xv_sz;
+      const float zn = sq[3 * cell_sz + me] + dz;
       a.z[idx] = zn;
-      a.x_out[idx] = fmaxf(xc - cur.tv * fmaf(dz, a.inv_p, zn), 0.f);
+      a.x_out[idx] = fmaxf(xc - sq[4 * cell_sz + me] * fmaf(dz, a.inv_p, zn), 0.f);
     }
     by_prev = b[1];
-    xc = xn;
-    vc = vn;
-    xn = xnn;
-    vn = vnn;
-    cur = nxt;
-    __syncthreads();
+    __syncthreads();  // stage iy % S is refilled by the next iteration's copy
   }
+  cp_async_wait<0>();
 }
 
 cudaError_t launch_prior(const DevGeom& g, const PriorArgs& a, cudaStream_t s) {
@@ -176,18 +178,27 @@ cudaError_t launch_prior(const DevGeom& g, const PriorArgs& a, cudaStream_t s) {
   if (zw > 16) return cudaErrorInvalidValue;
   const int cols = g.tune[SPDHG_TUNE_PRIOR_COLS] ? g.tune[SPDHG_TUNE_PRIOR_COLS]
                                                  : std::max(2, std::min(16 / zw, g.nx + 1));
-  const int ychunk = g.tune[SPDHG_TUNE_PRIOR_YCHUNK] ? g.tune[SPDHG_TUNE_PRIOR_YCHUNK] : 16;
-  if (cols * zw > 32) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)cols * zw * 33 * sizeof(float);
+  const int ychunk = g.tune[SPDHG_TUNE_PRIOR_YCHUNK] ? g.tune[SPDHG_TUNE_PRIOR_YCHUNK] : 64;
+  if (cols * zw > 16) return cudaErrorInvalidValue;
+  const int zc = zw * 32;
+  const size_t stage = (size_t)2 * (cols + 1) * zc + (size_t)5 * cols * zc;
+  const size_t smem = (kPriorStages * stage + 2 * (size_t)cols * zc) * sizeof(float);
   dim3 grid((g.nx + cols - 2) / (cols - 1), (g.ny + ychunk - 1) / ychunk);
   const int threads = cols * zw * 32;
+  auto launch = [&](auto kern) -> cudaError_t {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, threads, smem, s>>>(g, a, cols, ychunk);
+    return cudaGetLastError();
+  };
   switch (a.kind) {
-    case SPDHG_PRIOR_TV: k_prior<SPDHG_PRIOR_TV><<<grid, threads, smem, s>>>(g, a, cols, ychunk); break;
-    case SPDHG_PRIOR_DTV: k_prior<SPDHG_PRIOR_DTV><<<grid, threads, smem, s>>>(g, a, cols, ychunk); break;
-    case SPDHG_PRIOR_ATV: k_prior<SPDHG_PRIOR_ATV><<<grid, threads, smem, s>>>(g, a, cols, ychunk); break;
+    case SPDHG_PRIOR_TV: return launch(k_prior<SPDHG_PRIOR_TV>);
+    case SPDHG_PRIOR_DTV: return launch(k_prior<SPDHG_PRIOR_DTV>);
+    case SPDHG_PRIOR_ATV: return launch(k_prior<SPDHG_PRIOR_ATV>);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------
