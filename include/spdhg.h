@@ -126,7 +126,7 @@ int spdhg_set_data(spdhg_ctx* ctx, const float* b, const float* r, const float* 
                    const float* side, int where);
 
 /* y = P_i x on the bins of subset i (i = -1: all bins); bins of other subsets are not written.
- * x (N floats) and y (M floats) are device pointers in the documented layouts.  Uses mult of the
+ * x (N floats, 16-byte aligned) and y (M floats) are device pointers in the documented layouts.  Uses mult of the
  * last spdhg_set_data (ones if none). */
 int spdhg_project(spdhg_ctx* ctx, const float* x, float* y, int subset, void* stream);
 

@@ -355,6 +355,7 @@ int spdhg_set_data(spdhg_ctx* ctx, const float* b, const float* r, const float* 
 
 int spdhg_project(spdhg_ctx* ctx, const float* x, float* y, int subset, void* stream) {
   if (!ctx || !x || !y) return SPDHG_ERR_ARG;
+  if ((uintptr_t)x & 15) return fail(ctx, SPDHG_ERR_ARG, "x must be 16-byte aligned");
   if (subset < -1 || subset >= ctx->geom.n_subsets) return fail(ctx, SPDHG_ERR_ARG, "subset out of range");
   if (int st = check_device(ctx)) return st;
   FwdArgs a{};
@@ -678,9 +679,10 @@ int spdhg_objective(spdhg_ctx* ctx, const float* x, int where, double out[3], vo
   if (!x) {
     if (!ctx->is_setup) return fail(ctx, SPDHG_ERR_STATE, "no iterate before spdhg_setup");
     xd = ctx->x[ctx->xcur];
-  } else if (where == SPDHG_WHERE_HOST) {
+  } else if (where == SPDHG_WHERE_HOST || ((uintptr_t)x & 15)) {
     CK(dalloc(&ctx->tmp_img, N));
-    CK(cudaMemcpyAsync(ctx->tmp_img, x, N * sizeof(float), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->tmp_img, x, N * sizeof(float),
+                       where == SPDHG_WHERE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     xd = ctx->tmp_img;
   }
   FwdArgs a{};

@@ -139,6 +139,19 @@ __device__ __forceinline__ int segment_taps(const DevGeom& g, int r, int gi, con
 // forward projection: one block per transaxial line (view, radial bin), threads over planes
 // ---------------------------------------------------------------------------------------
 
+// Asynchronous global -> shared copies (4 and 16 bytes).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 struct Entry {
   int col;  // iy * nx + ix
   PixInt I;
@@ -182,14 +195,17 @@ __device__ __forceinline__ int row_entries(const DevGeom& g, const Line& L, bool
 }
 
 template <int NT, int PPT, int MODE>
-__global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc, int split, FwdArgs a) {
+__global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc, int split, int xs_stride,
+                                                 FwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int warp_tot[2];
   __shared__ int n_ent_sh;
   const int cap = kCandPerRow * rpc;
-  Entry* ent = reinterpret_cast<Entry*>(smem);
+  float* xs = reinterpret_cast<float*>(smem);      // staged x columns: [entry][xs_stride]
+  Entry* ent = reinterpret_cast<Entry*>(xs + (size_t)cap * xs_stride);
   int* tapJ = reinterpret_cast<int*>(ent + cap);   // j0 | (nt << 24) per (segment, entry)
   float* tapL = reinterpret_cast<float*>(tapJ + g.n_seg * cap);
+  const int nimg = g.nx * g.ny * g.nz;
 
   // block = (line, part): `split` blocks share the planes of one LOR line
   const int line = blockIdx.x / split, part = blockIdx.x - line * split;
@@ -245,6 +261,23 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc,
     }
     __syncthreads();
     const int n_ent = n_ent_sh;
+    // 1b. stage the x columns of the entries (16-byte copies of the aligned cover of each
+    //     column; 4-byte copies at the end of the image), overlapped with the taps below
+    {
+      const int chunks = xs_stride / 4;
+      for (int i = threadIdx.x; i < n_ent * chunks; i += blockDim.x) {
+        const int e = i / chunks, k = i - e * chunks;
+        const int gbase = (ent[e].col * nz) & ~3;
+        const int gi0 = gbase + 4 * k;
+        float* dst = xs + e * xs_stride + 4 * k;
+        if (gi0 + 4 <= nimg) {
+          cp_async16(dst, a.x + gi0);
+        } else {
+          for (int q = 0; q < 4; ++q)
+            if (gi0 + q < nimg) cp_async4(dst + q, a.x + gi0 + q);
+        }
+      }
+    }
     // 2. axial taps of every (entry, segment of this block's planes)
     for (int it = threadIdx.x; it < nseg_part * n_ent; it += blockDim.x) {
       const int gi = g_lo + it / n_ent, e = it - (it / n_ent) * n_ent;
@@ -257,10 +290,11 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc,
 #pragma unroll
       for (int k = 0; k < NT; ++k) tapL[slot * NT + k] = Lk[k];
     }
+    cp_async_commit_wait_all();
     __syncthreads();
     // 3. accumulate the planes of this thread over the entries
     for (int e = 0; e < n_ent; ++e) {
-      const float* __restrict__ xc = a.x + (size_t)ent[e].col * nz;
+      const float* xc = xs + e * xs_stride + ((ent[e].col * nz) & 3);
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         if (pseg[k] < 0) continue;
@@ -274,7 +308,7 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc,
             const float Lt = tapL[slot * NT + t];
             const int izt = iz - t;
             if ((unsigned)izt < (unsigned)nz) {
-              acc[k] = fmaf(Lt, __ldg(xc + izt), acc[k]);
+              acc[k] = fmaf(Lt, xc[izt], acc[k]);
               if (MODE != FWD_PROJECT) chord[k] += Lt;
             }
           }
@@ -318,116 +352,133 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc,
 // backprojection: one thread group per voxel column (ix, iy), threads over iz
 // ---------------------------------------------------------------------------------------
 
-template <int NT>
-struct Item {
-  int base;  // subset-local sinogram index of (view, radial, first plane of the segment)
-  int n;     // planes in the segment
-  int j0;
-  int nt;    // taps actually used (trailing zero-length taps dropped)
-  float L[NT];
-};
-
 struct PixItem {
   int l, r;  // view (subset-local) and radial bin
   PixInt I;
 };
 
-// Candidate (view, bin) pairs of the pixel footprint handled per chunk by the first warp of a
-// column; the pairs that intersect the pixel are compacted with a warp ballot.
-constexpr int kPairsPerChunk = 32;
+constexpr int kBwdTile = 4;              // block = kBwdTile x kBwdTile voxel columns, one warp each
+constexpr int kBwdWarps = kBwdTile * kBwdTile;
+constexpr int kBwdMaxItems = 64;         // (pair, segment) items per column and view
 
-template <int NT, int MODE>
-__global__ void __launch_bounds__(256) k_backward(DevGeom g, int subset, int tpc, int cpb, int vchunk,
-                                                  BwdArgs a) {
+// Backprojection.  A block owns a 4 x 4 tile of voxel columns; for each view of the subset it
+// stages the contiguous radial rows w[view][r_min..r_max][0..P) that the tile's footprints
+// touch into shared memory (cp.async, overlapped with the geometry below).  Each warp owns one
+// column: its lanes find the footprint (bin, pixel interval) pairs, compact them with a ballot,
+// compute the axial taps of every (pair, segment) item, and then gather along contiguous
+// plane runs from shared memory, lane = iz mod 32, ZK voxels per lane.
+template <int NT, int ZK, int MODE>
+__global__ void __launch_bounds__(kBwdWarps * 32) k_backward(DevGeom g, int subset, int nr_tile, BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int n_pairs_sh[8];
-  const int items_per_col = kPairsPerChunk * g.n_seg;
-  const int cb = threadIdx.x / tpc;
-  PixItem* pix = reinterpret_cast<PixItem*>(smem) + cb * kPairsPerChunk;
-  Item<NT>* items = reinterpret_cast<Item<NT>*>(reinterpret_cast<PixItem*>(smem) + cpb * kPairsPerChunk) +
-                    cb * items_per_col;
-  const int tz = threadIdx.x % tpc;
-  const int col = blockIdx.x * cpb + cb;
-  const bool live = col < g.nx * g.ny;
-  const int iy = live ? col / g.nx : 0, ix = live ? col - iy * g.nx : 0;
-  const int nviews = subset_views(g, subset);
+  float* sw = reinterpret_cast<float*>(smem);                                  // nr_tile x P
+  float4* itL = reinterpret_cast<float4*>(sw + ((nr_tile * g.P + 3) & ~3));    // [warp][item]
+  int4* itM = reinterpret_cast<int4*>(itL + kBwdWarps * kBwdMaxItems);
+  PixItem* pix = reinterpret_cast<PixItem*>(itM + kBwdWarps * kBwdMaxItems);  // [warp][32]
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int tx0 = blockIdx.x * kBwdTile, ty0 = blockIdx.y * kBwdTile;
+  const int ix = tx0 + (wi % kBwdTile), iy = ty0 + (wi / kBwdTile);
+  const bool live = ix < g.nx && iy < g.ny;
   const float Xc = (float)ix + 0.5f - 0.5f * (float)g.nx;
   const float Yc = (float)iy + 0.5f - 0.5f * (float)g.ny;
+  const float X0 = (float)tx0 + 0.5f - 0.5f * (float)g.nx, Y0 = (float)ty0 + 0.5f - 0.5f * (float)g.ny;
+  const float X1 = X0 + (float)(kBwdTile - 1), Y1 = Y0 + (float)(kBwdTile - 1);
+  float4* myL = itL + wi * kBwdMaxItems;
+  int4* myM = itM + wi * kBwdMaxItems;
+  PixItem* mypix = pix + wi * 32;
+  const int nviews = subset_views(g, subset);
   const int nz = g.nz;
-  float acc = 0.f;  // tpc >= nz: one voxel per thread
-
-  for (int l0 = 0; l0 < nviews; l0 += vchunk) {
-    const int nv = min(vchunk, nviews - l0);
-    // 1. footprint pairs -> exact pixel intervals, compacted (first warp of the column)
-    if (tz < 32) {
-      PixItem P;
-      bool ok = false;
-      if (live && tz < nv * g.nr_max) {
-        const int l = l0 + tz / g.nr_max, ri = tz % g.nr_max;
-        const int v = subset_view(g, subset, l);
-        const float4 cs = g.view[v];
-        const float sc = Xc * cs.x + Yc * cs.z;
-        const float hw = 0.5f * (fabsf(cs.x) + fabsf(cs.z));
-        const int rlo = (int)ceilf((sc - hw) * g.inv_drp + g.half_R) - 1;
-        const int rhi = (int)floorf((sc + hw) * g.inv_drp + g.half_R) + 1;
-        const int r = rlo + ri;
-        if (r >= 0 && r < g.R && r <= rhi) {
-          const Line L = make_line(g, v, r);
-          ok = pixel_interval(g, L, ix, iy, P.I);
-          P.l = l;
-          P.r = r;
-        }
-      }
-      const unsigned mask = __ballot_sync(0xffffffffu, ok);
-      if (ok) pix[__popc(mask & ((1u << tz) - 1u))] = P;
-      if (tz == 0) n_pairs_sh[cb] = __popc(mask);
-    }
-    __syncthreads();
-    const int np = n_pairs_sh[cb];
-    // 2. axial taps per (pair, segment)
-    for (int it = tz; it < np * g.n_seg; it += tpc) {
-      const int pi = it / g.n_seg, gi = it - pi * g.n_seg;
-      const PixItem P = pix[pi];
-      Item<NT> I;
-      I.j0 = segment_taps<NT>(g, P.r, gi, P.I, I.L);
-      I.base = (P.l * g.R + P.r) * g.P + g.seg[gi].p0;
-      I.n = g.seg[gi].n;
-      int nt = NT;
-      while (nt > 1 && I.L[nt - 1] == 0.f) --nt;
-      I.nt = nt;
-      items[it] = I;
-    }
-    __syncthreads();
-    // 3. gather along contiguous plane runs
-    if (live && tz < nz) {
-      const int ni = np * g.n_seg;
-      for (int it = 0; it < ni; ++it) {
-        const Item<NT> I = items[it];
-        const int q = tz + I.j0;
-        const float* __restrict__ wp = a.w + I.base;
+  float acc[ZK];
 #pragma unroll
-        for (int k = 0; k < NT; ++k) {
-          if (k < I.nt) {
-            const int qk = q + k;
-            if ((unsigned)qk < (unsigned)I.n) acc = fmaf(I.L[k], __ldg(wp + qk), acc);
+  for (int k = 0; k < ZK; ++k) acc[k] = 0.f;
+
+  for (int l = 0; l < nviews; ++l) {
+    const int v = subset_view(g, subset, l);
+    const float4 cs = g.view[v];
+    const float hw = 0.5f * (fabsf(cs.x) + fabsf(cs.z));
+    // radial rows of the whole tile (footprints of its extreme pixel centres)
+    const float s00 = X0 * cs.x + Y0 * cs.z, s01 = X0 * cs.x + Y1 * cs.z;
+    const float s10 = X1 * cs.x + Y0 * cs.z, s11 = X1 * cs.x + Y1 * cs.z;
+    const float smin = fminf(fminf(s00, s01), fminf(s10, s11)), smax = fmaxf(fmaxf(s00, s01), fmaxf(s10, s11));
+    const int r_min = max(0, (int)ceilf((smin - hw) * g.inv_drp + g.half_R) - 1);
+    const int r_max = min(g.R - 1, min(r_min + nr_tile - 1, (int)floorf((smax + hw) * g.inv_drp + g.half_R) + 1));
+    // 1. stage rows r_min..r_max of this view (contiguous)
+    {
+      const float* src = a.w + ((size_t)l * g.R + r_min) * g.P;
+      const int n = (r_max - r_min + 1) * g.P;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) cp_async4(sw + i, src + i);
+    }
+    // 2. footprint pairs of this warp's column (overlaps the copy)
+    PixItem P;
+    bool ok = false;
+    if (live && lane < g.nr_max) {
+      const float sc = Xc * cs.x + Yc * cs.z;
+      const int rlo = (int)ceilf((sc - hw) * g.inv_drp + g.half_R) - 1;
+      const int rhi = (int)floorf((sc + hw) * g.inv_drp + g.half_R) + 1;
+      const int r = rlo + lane;
+      if (r >= r_min && r <= r_max && r <= rhi) {
+        const Line L = make_line(g, v, r);
+        ok = pixel_interval(g, L, ix, iy, P.I);
+        P.l = l;
+        P.r = r;
+      }
+    }
+    const unsigned mask = __ballot_sync(0xffffffffu, ok);
+    if (ok) mypix[__popc(mask & ((1u << lane) - 1u))] = P;
+    const int np = __popc(mask);
+    __syncwarp();
+    // 3. axial taps per (pair, segment)
+    const int ni = min(np * g.n_seg, kBwdMaxItems);
+    for (int it = lane; it < ni; it += 32) {
+      const int pi = it / g.n_seg, gi = it - pi * g.n_seg;
+      const PixItem Q = mypix[pi];
+      float Lk[NT];
+      const int j0 = segment_taps<NT>(g, Q.r, gi, Q.I, Lk);
+      int nt = NT;
+      while (nt > 1 && Lk[nt - 1] == 0.f) --nt;
+      const SegDev sd = g.seg[gi];
+      float4 Lv = make_float4(Lk[0], NT > 1 ? Lk[1] : 0.f, NT > 2 ? Lk[2] : 0.f, NT > 3 ? Lk[3] : 0.f);
+      myL[it] = Lv;
+      // smem index of (iz, tap t): a + iz + t, valid while lo <= iz + t < hi
+      myM[it] = make_int4((Q.r - r_min) * g.P + sd.p0 + j0, -j0, sd.n - j0, nt);
+    }
+    cp_async_commit_wait_all();
+    __syncthreads();
+    // 4. gather
+    if (live) {
+      for (int it = 0; it < ni; ++it) {
+        const float4 Lv = myL[it];
+        const int4 M = myM[it];
+        const float Lt[4] = {Lv.x, Lv.y, Lv.z, Lv.w};
+        const unsigned span = (unsigned)(M.z - M.y);
+#pragma unroll
+        for (int k = 0; k < ZK; ++k) {
+          const int iz = lane + 32 * k;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            if (t < M.w && (unsigned)(iz + t - M.y) < span) acc[k] = fmaf(Lt[t], sw[M.x + iz + t], acc[k]);
           }
         }
       }
     }
-    __syncthreads();
+    __syncthreads();  // the staged rows are replaced by the next view's
   }
-  if (!live || tz >= nz) return;
-  const size_t idx = (size_t)col * nz + tz;
-  if (MODE == BWD_OUT) {
-    a.out[idx] = acc;
-  } else if (MODE == BWD_SENS) {
-    // T_i = rho p_i / (gamma (P_i^T 1)); +inf (kept) where the subset does not see the voxel
-    if (acc > 0.f) a.T[idx] = fminf(a.T[idx], a.sens_num / acc);
-  } else {
-    // z = z + dz;  zbar = z + dz / p_i;  next primal step x = max(x - T zbar, 0)
-    const float zn = a.z[idx] + acc;
-    a.z[idx] = zn;
-    a.x[idx] = fmaxf(a.x[idx] - a.T[idx] * fmaf(acc, a.inv_p, zn), 0.f);
+  if (!live) return;
+#pragma unroll
+  for (int k = 0; k < ZK; ++k) {
+    const int iz = lane + 32 * k;
+    if (iz >= nz) continue;
+    const size_t idx = ((size_t)iy * g.nx + ix) * nz + iz;
+    if (MODE == BWD_OUT) {
+      a.out[idx] = acc[k];
+    } else if (MODE == BWD_SENS) {
+      // T_i = rho p_i / (gamma (P_i^T 1)); +inf (kept) where the subset does not see the voxel
+      if (acc[k] > 0.f) a.T[idx] = fminf(a.T[idx], a.sens_num / acc[k]);
+    } else {
+      // z = z + dz;  zbar = z + dz / p_i;  next primal step x = max(x - T zbar, 0)
+      const float zn = a.z[idx] + acc[k];
+      a.z[idx] = zn;
+      a.x[idx] = fmaxf(a.x[idx] - a.T[idx] * fmaf(acc[k], a.inv_p, zn), 0.f);
+    }
   }
 }
 
@@ -448,7 +499,7 @@ __global__ void k_gather_subset(DevGeom g, int subset, const float* __restrict__
 
 static int fwd_split(const DevGeom& g) {
   if (g.tune[SPDHG_TUNE_FWD_SPLIT]) return g.tune[SPDHG_TUNE_FWD_SPLIT];
-  return g.P >= 512 ? 4 : (g.P >= 256 ? 2 : 1);  // enough blocks per SM for long plane lists
+  return 1;
 }
 
 static int fwd_threads(int planes, int* ppt) {
@@ -462,12 +513,15 @@ static int fwd_threads(int planes, int* ppt) {
 
 template <int NT, int PPT, int MODE>
 static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cudaStream_t s, int threads, int split) {
+  // x column of nz floats staged as the 16-byte aligned cover: ceil((nz + 3) / 4) * 4 floats
+  const int xs_stride = ((g.nz + 3 + 3) / 4) * 4;
   auto bytes = [&](int rows) {
     const size_t cap = (size_t)kCandPerRow * rows;
-    return cap * (sizeof(Entry) + (size_t)g.n_seg * sizeof(int) + (size_t)g.n_seg * NT * sizeof(float));
+    return cap * ((size_t)xs_stride * sizeof(float) + sizeof(Entry) + (size_t)g.n_seg * sizeof(int) +
+                  (size_t)g.n_seg * NT * sizeof(float));
   };
   int rpc = 64;
-  while (rpc > 8 && bytes(rpc) > 40 * 1024) rpc /= 2;
+  while (rpc > 8 && bytes(rpc) > 72 * 1024) rpc /= 2;
   const size_t smem = bytes(rpc);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_forward<NT, PPT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -475,7 +529,7 @@ static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cu
   }
   const int lines = subset_views(g, subset) * g.R;
   if (lines == 0) return cudaSuccess;
-  k_forward<NT, PPT, MODE><<<lines * split, threads, smem, s>>>(g, subset, rpc, split, a);
+  k_forward<NT, PPT, MODE><<<lines * split, threads, smem, s>>>(g, subset, rpc, split, xs_stride, a);
   return cudaGetLastError();
 }
 
@@ -514,34 +568,48 @@ cudaError_t launch_forward(const DevGeom& g, int subset, int mode, const FwdArgs
   }
 }
 
-template <int NT, int MODE>
+static int bwd_rows_per_tile(const DevGeom& g) {
+  // radial rows a tile's footprints can touch: spread of the tile centres plus one footprint
+  return (int)floorf((2.f * (kBwdTile - 1) + 1.4143f) * g.inv_drp) + 4;
+}
+
+template <int NT, int ZK, int MODE>
 static cudaError_t bwd_launch(const DevGeom& g, int subset, const BwdArgs& a, cudaStream_t s) {
-  int tpc = ((g.nz + 31) / 32) * 32;
-  if (tpc > 256) return cudaErrorInvalidValue;
-  int cpb = tpc >= 128 ? 1 : 256 / tpc;
-  if (g.tune[SPDHG_TUNE_BWD_COLS] && g.tune[SPDHG_TUNE_BWD_COLS] * tpc <= 256) cpb = g.tune[SPDHG_TUNE_BWD_COLS];
-  int vchunk = kPairsPerChunk / g.nr_max;  // views whose footprint pairs fit one warp
-  if (vchunk < 1) return cudaErrorInvalidValue;
-  const int nviews = subset_views(g, subset);
-  if (vchunk > nviews) vchunk = nviews > 0 ? nviews : 1;
-  const size_t smem = (size_t)cpb * kPairsPerChunk * (sizeof(PixItem) + (size_t)g.n_seg * sizeof(Item<NT>));
+  // at most floor(sqrt(2) vx / d_radial) + 2 bins of one view cross a pixel
+  const int max_pairs = (int)floorf(1.4143f * g.inv_drp) + 2;
+  if (g.nr_max > 32 || max_pairs * g.n_seg > kBwdMaxItems) return cudaErrorInvalidValue;
+  const int nr_tile = bwd_rows_per_tile(g);
+  const size_t sw_floats = ((size_t)nr_tile * g.P + 3) & ~(size_t)3;
+  const size_t smem = sw_floats * sizeof(float) + (size_t)kBwdWarps * kBwdMaxItems * (sizeof(float4) + sizeof(int4)) +
+                      (size_t)kBwdWarps * 32 * sizeof(PixItem);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  auto kern = k_backward<NT, ZK, MODE>;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_backward<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const int cols = g.nx * g.ny;
-  const int blocks = (cols + cpb - 1) / cpb;
-  k_backward<NT, MODE><<<blocks, cpb * tpc, smem, s>>>(g, subset, tpc, cpb, vchunk, a);
+  dim3 grid((g.nx + kBwdTile - 1) / kBwdTile, (g.ny + kBwdTile - 1) / kBwdTile);
+  kern<<<grid, kBwdWarps * 32, smem, s>>>(g, subset, nr_tile, a);
   return cudaGetLastError();
+}
+
+template <int NT, int MODE>
+static cudaError_t bwd_zk(const DevGeom& g, int subset, const BwdArgs& a, cudaStream_t s) {
+  const int zk = (g.nz + 31) / 32;
+  if (zk <= 1) return bwd_launch<NT, 1, MODE>(g, subset, a, s);
+  if (zk <= 2) return bwd_launch<NT, 2, MODE>(g, subset, a, s);
+  if (zk <= 4) return bwd_launch<NT, 4, MODE>(g, subset, a, s);
+  if (zk <= 8) return bwd_launch<NT, 8, MODE>(g, subset, a, s);
+  return cudaErrorInvalidValue;
 }
 
 template <int MODE>
 static cudaError_t bwd_nt(const DevGeom& g, int subset, const BwdArgs& a, cudaStream_t s) {
   switch (g.taps) {
-    case 1: return bwd_launch<1, MODE>(g, subset, a, s);
-    case 2: return bwd_launch<2, MODE>(g, subset, a, s);
-    case 3: return bwd_launch<3, MODE>(g, subset, a, s);
-    case 4: return bwd_launch<4, MODE>(g, subset, a, s);
+    case 1: return bwd_zk<1, MODE>(g, subset, a, s);
+    case 2: return bwd_zk<2, MODE>(g, subset, a, s);
+    case 3: return bwd_zk<3, MODE>(g, subset, a, s);
+    case 4: return bwd_zk<4, MODE>(g, subset, a, s);
     default: return cudaErrorInvalidValue;
   }
 }
