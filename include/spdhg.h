@@ -126,15 +126,15 @@ int spdhg_set_data(spdhg_ctx* ctx, const float* b, const float* r, const float* 
                    const float* side, int where);
 
 /* y = P_i x on the bins of subset i (i = -1: all bins); bins of other subsets are not written.
- * x (N floats, 16-byte aligned) and y (M floats) are device pointers in the documented layouts.  Uses mult of the
+ * x (N floats) and y (M floats) are device pointers in the documented layouts.  Uses mult of the
  * last spdhg_set_data (ones if none). */
 int spdhg_project(spdhg_ctx* ctx, const float* x, float* y, int subset, void* stream);
 
 /* x = P_i^T y restricted to the bins of subset i (i = -1: all bins); device pointers. */
 int spdhg_backproject(spdhg_ctx* ctx, const float* y, float* x, int subset, void* stream);
 
-/* Step sizes and initial state for `params`: sigma_j = gamma rho / (P_i 1)_j (recomputed inside
- * the projector), T = min_i T_i with T_i = rho p_i / (gamma P_i^T 1) for data blocks and the
+/* Step sizes and initial state for `params`: sigma_j = gamma rho / (P_i 1)_j for every bin
+ * (stored), T = min_i T_i with T_i = rho p_i / (gamma P_i^T 1) for data blocks and the
  * scalar form for prior blocks; T = 0 where no block sees a voxel.  x = max(x0, 0) (the first
  * primal step of Algorithm 2 with zbar = 0), y = 0, z = 0, prior duals 0.  x0 = NULL: zeros. */
 int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int where,

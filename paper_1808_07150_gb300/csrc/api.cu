@@ -152,6 +152,35 @@ int copy_out(spdhg_ctx* ctx, void* dst, const float* src, int64_t n, int where, 
   return SPDHG_OK;
 }
 
+// Row-split scratch of the forward projector for `subset` (allocated on first need).
+int prepare_forward(spdhg_ctx* ctx, int subset, FwdArgs& a, cudaStream_t s) {
+  const int split = forward_split(ctx->dg, subset);
+  if (split <= 1) return SPDHG_OK;
+  const size_t lines = (size_t)subset_views(ctx->dg, subset) * ctx->dg.R;
+  const size_t need = lines * split * ctx->dg.P;
+  if (need > ctx->fwd_part_cap) {
+    if (ctx->fwd_part) cudaFree(ctx->fwd_part);
+    ctx->fwd_part = nullptr;
+    ctx->fwd_part_cap = 0;
+    CK(cudaMalloc(&ctx->fwd_part, 2 * need * sizeof(float)));
+    ctx->fwd_part_cap = need;
+  }
+  if (lines > ctx->fwd_ticket_cap) {
+    if (ctx->fwd_tickets) cudaFree(ctx->fwd_tickets);
+    ctx->fwd_tickets = nullptr;
+    ctx->fwd_ticket_cap = 0;
+    CK(cudaMalloc(&ctx->fwd_tickets, lines * sizeof(unsigned)));
+    CK(cudaMemsetAsync(ctx->fwd_tickets, 0, lines * sizeof(unsigned), s));
+    ctx->fwd_ticket_cap = lines;
+  }
+  a.part_acc = ctx->fwd_part;
+  a.part_chord = ctx->fwd_part + ctx->fwd_part_cap;
+  a.tickets = ctx->fwd_tickets;
+  a.part_cap = ctx->fwd_part_cap;
+  a.ticket_cap = ctx->fwd_ticket_cap;
+  return SPDHG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -179,6 +208,11 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
     kappa_max = std::max(kappa_max, fabs(g.seg_dz[k]) / (2.0 * hmin * g.vz));
   }
   if (P > 512 * kMaxPlanesPerThread) return SPDHG_ERR_UNSUPPORTED;
+  {
+    int n_runs = 0;
+    for (int k = 0; k < g.n_segments; ++k) n_runs += (g.seg_n[k] + 31) / 32;
+    if (n_runs > 64) return SPDHG_ERR_UNSUPPORTED;  // the forward kernel holds <= 4 runs per warp, 16 warps
+  }
   // kernels index images (up to 6 components) and sinograms with 32-bit integers
   if ((double)g.nx * g.ny * g.nz * 6 >= 2147483647.0 || (double)g.n_views * g.n_radial * P >= 2147483647.0)
     return SPDHG_ERR_UNSUPPORTED;
@@ -247,6 +281,9 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
     for (int q = 0; q < g.seg_n[k]; ++q) plane_seg[p0 + q] = k;
     p0 += g.seg_n[k];
   }
+  std::vector<int2> runs;
+  for (int k = 0; k < S; ++k)
+    for (int q0 = 0; q0 < g.seg_n[k]; q0 += 32) runs.push_back(make_int2(k, q0));
   auto cleanup_fail = [&](cudaError_t e) {
     spdhg_destroy(ctx);
     return e == cudaErrorMemoryAllocation ? SPDHG_ERR_OOM : SPDHG_ERR_CUDA;
@@ -262,6 +299,8 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   if ((e = cudaMemcpy(ctx->d_rs, rs.data(), sizeof(float4) * R * S, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_seg, seg.data(), sizeof(SegDev) * S, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_plane_seg, plane_seg.data(), sizeof(int) * P, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMalloc(&ctx->d_runs, sizeof(int2) * runs.size())) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMemcpy(ctx->d_runs, runs.data(), sizeof(int2) * runs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
 
   DevGeom& d = ctx->dg;
   d.nx = g.nx;
@@ -281,15 +320,17 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   d.rs = ctx->d_rs;
   d.seg = ctx->d_seg;
   d.plane_seg = ctx->d_plane_seg;
+  d.n_runs = (int)runs.size();
+  d.runs = ctx->d_runs;
   *out = ctx;
   return SPDHG_OK;
 }
 
 void spdhg_destroy(spdhg_ctx* ctx) {
   if (!ctx) return;
-  void* ptrs[] = {ctx->d_view, ctx->d_rad, ctx->d_rs, ctx->d_seg, ctx->d_plane_seg, ctx->b, ctx->r, ctx->mult, ctx->side,
-                  ctx->x[0], ctx->x[1], ctx->z, ctx->T, ctx->y, ctx->wdy, ctx->q[0], ctx->q[1],
-                  ctx->w[0], ctx->w[1], ctx->zw, ctx->q2[0], ctx->q2[1], ctx->tmp_sino, ctx->tmp_img,
+  void* ptrs[] = {ctx->d_view, ctx->d_rad, ctx->d_rs, ctx->d_runs, ctx->d_seg, ctx->d_plane_seg, ctx->b, ctx->r, ctx->mult, ctx->side,
+                  ctx->x[0], ctx->x[1], ctx->z, ctx->T, ctx->y, ctx->sigma, ctx->wdy, ctx->q[0], ctx->q[1],
+                  ctx->w[0], ctx->w[1], ctx->zw, ctx->q2[0], ctx->q2[1], ctx->tmp_sino, ctx->tmp_img, ctx->fwd_part, ctx->fwd_tickets,
                   ctx->red, ctx->red_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -355,13 +396,13 @@ int spdhg_set_data(spdhg_ctx* ctx, const float* b, const float* r, const float* 
 
 int spdhg_project(spdhg_ctx* ctx, const float* x, float* y, int subset, void* stream) {
   if (!ctx || !x || !y) return SPDHG_ERR_ARG;
-  if ((uintptr_t)x & 15) return fail(ctx, SPDHG_ERR_ARG, "x must be 16-byte aligned");
   if (subset < -1 || subset >= ctx->geom.n_subsets) return fail(ctx, SPDHG_ERR_ARG, "subset out of range");
   if (int st = check_device(ctx)) return st;
   FwdArgs a{};
   a.x = x;
   a.out = y;
   a.mult = ctx->has_mult ? ctx->mult : nullptr;
+  if (int st = prepare_forward(ctx, subset, a, (cudaStream_t)stream)) return st;
   CK(launch_forward(ctx->dg, subset, FWD_PROJECT, a, (cudaStream_t)stream));
   return SPDHG_OK;
 }
@@ -438,6 +479,7 @@ int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int
   CK(dalloc(&ctx->z, N));
   CK(dalloc(&ctx->T, N));
   CK(dalloc(&ctx->y, M));
+  CK(dalloc(&ctx->sigma, M));
   CK(dalloc(&ctx->wdy, ctx->max_subset_bins));
   const bool tgv = p.prior == SPDHG_PRIOR_TGV;
   if (p.prior != SPDHG_PRIOR_NONE) {
@@ -487,6 +529,16 @@ int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int
   }
   k_finalize_T<<<grid_for(N), 256, 0, s>>>(ctx->T, N, t_prior);
   CK(cudaGetLastError());
+  // sigma_j = gamma rho / (P 1)_j for every bin (Eq. EQU:STEPSIZE:PRECOND), stored once
+  {
+    FwdArgs a{};
+    a.x = ctx->x[0];  // unused by the sigma pass
+    a.out = ctx->sigma;
+    a.mult = ctx->has_mult ? ctx->mult : nullptr;
+    a.gamma_rho = (float)(p.gamma * p.rho);
+    if (int st = prepare_forward(ctx, -1, a, s)) return st;
+    CK(launch_forward(ctx->dg, -1, FWD_SIGMA, a, s));
+  }
 
   if (p.prior == SPDHG_PRIOR_DTV) {
     CK(launch_side_max_grad(ctx->dg, ctx->side, ctx->red, ctx->red_blocks, ctx->red_out, s));
@@ -546,7 +598,9 @@ int spdhg_iterate(spdhg_ctx* ctx, const int32_t* blocks, int n, void* stream) {
       fa.r = ctx->r;
       fa.y = ctx->y;
       fa.wdy = ctx->wdy;
+      fa.sigma = ctx->sigma;
       fa.gamma_rho = (float)(p.gamma * p.rho);
+      if (int st = prepare_forward(ctx, i, fa, s)) return st;
       {
         ProfScope ps(ctx, SPDHG_KERNEL_FORWARD, s);
         CK(launch_forward(ctx->dg, i, FWD_DATA, fa, s));
@@ -647,23 +701,7 @@ int spdhg_get(spdhg_ctx* ctx, int what, void* dst, int where, void* stream) {
     case SPDHG_STATE_Q2:
       if (!tgv) return fail(ctx, SPDHG_ERR_STATE, "no TGV state");
       return copy_out(ctx, dst, ctx->q2[ctx->q2cur], 6 * N, where, s);
-    case SPDHG_STATE_SIGMA: {
-      float* out = nullptr;
-      if (where == SPDHG_WHERE_DEVICE) {
-        out = (float*)dst;
-      } else {
-        CK(dalloc(&ctx->tmp_sino, M));
-        out = ctx->tmp_sino;
-      }
-      FwdArgs a{};
-      a.x = ctx->x[ctx->xcur];  // unused by the sigma pass except as a valid pointer
-      a.out = out;
-      a.mult = ctx->has_mult ? ctx->mult : nullptr;
-      a.gamma_rho = (float)(ctx->params.gamma * ctx->params.rho);
-      CK(launch_forward(ctx->dg, -1, FWD_SIGMA, a, s));
-      if (where == SPDHG_WHERE_HOST) return copy_out(ctx, dst, out, M, where, s);
-      return SPDHG_OK;
-    }
+    case SPDHG_STATE_SIGMA: return copy_out(ctx, dst, ctx->sigma, M, where, s);
     default: return fail(ctx, SPDHG_ERR_ARG, "unknown state array");
   }
 }
@@ -679,7 +717,7 @@ int spdhg_objective(spdhg_ctx* ctx, const float* x, int where, double out[3], vo
   if (!x) {
     if (!ctx->is_setup) return fail(ctx, SPDHG_ERR_STATE, "no iterate before spdhg_setup");
     xd = ctx->x[ctx->xcur];
-  } else if (where == SPDHG_WHERE_HOST || ((uintptr_t)x & 15)) {
+  } else if (where == SPDHG_WHERE_HOST) {
     CK(dalloc(&ctx->tmp_img, N));
     CK(cudaMemcpyAsync(ctx->tmp_img, x, N * sizeof(float),
                        where == SPDHG_WHERE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
@@ -689,6 +727,7 @@ int spdhg_objective(spdhg_ctx* ctx, const float* x, int where, double out[3], vo
   a.x = xd;
   a.out = ctx->tmp_sino;
   a.mult = ctx->has_mult ? ctx->mult : nullptr;
+  if (int st = prepare_forward(ctx, -1, a, s)) return st;
   CK(launch_forward(ctx->dg, -1, FWD_PROJECT, a, s));
   CK(launch_data_term(ctx->tmp_sino, ctx->b, ctx->r, M, ctx->red, ctx->red_blocks, ctx->red_out, s));
   int kind = ctx->is_setup ? ctx->params.prior : SPDHG_PRIOR_NONE;

@@ -40,6 +40,8 @@ struct DevGeom {
   const float4* rs;      // per (radial bin, segment): kappa_hi, kappa_lo, len_scale, 0
   const SegDev* seg;
   const int* plane_seg;  // plane -> segment
+  int n_runs;            // warp-sized plane runs: run k = planes [q0, q0 + 32) of one segment
+  const int2* runs;      // (segment, q0) per run
   int tune[SPDHG_TUNE_KNOBS];  // launch-shape overrides (0: built-in heuristic)
 };
 
@@ -68,8 +70,17 @@ struct FwdArgs {
   const float* r;
   float* y;              // dual, full sinogram
   float* wdy;            // subset-local mult * (y+ - y)
+  const float* sigma;    // FWD_DATA: per-bin dual step sigma_j (full sinogram)
   float gamma_rho;       // gamma * rho
+  // row-split scratch: partial plane sums [line][part][P] and one ticket per line (zeroed)
+  float* part_acc;
+  float* part_chord;
+  unsigned* tickets;
+  size_t part_cap;       // floats in each partial buffer
+  size_t ticket_cap;     // tickets
 };
+// blocks per LOR line the forward projector uses for `subset` (1: no scratch needed)
+int forward_split(const DevGeom& g, int subset);
 
 struct BwdArgs {
   const float* w;        // subset-local sinogram (mult already applied)
@@ -141,6 +152,7 @@ struct spdhg_ctx {
   float4* d_view = nullptr;
   float4* d_rad = nullptr;
   float4* d_rs = nullptr;
+  int2* d_runs = nullptr;
   spdhg::SegDev* d_seg = nullptr;
   int* d_plane_seg = nullptr;
   // data
@@ -150,6 +162,7 @@ struct spdhg_ctx {
   float* x[2] = {nullptr, nullptr};
   int xcur = 0;
   float *z = nullptr, *T = nullptr, *y = nullptr, *wdy = nullptr;
+  float* sigma = nullptr;      // per-bin dual step sigma_j, computed by spdhg_setup
   float* q[2] = {nullptr, nullptr};
   int qcur = 0;
   // TGV
@@ -162,6 +175,9 @@ struct spdhg_ctx {
   // scratch
   float* tmp_sino = nullptr;   // M floats (objective, sigma export)
   float* tmp_img = nullptr;    // N floats (objective of a host image)
+  float* fwd_part = nullptr;   // forward row-split partial sums (2 x fwd_part_cap floats)
+  unsigned* fwd_tickets = nullptr;
+  size_t fwd_part_cap = 0, fwd_ticket_cap = 0;
   double* red = nullptr;       // FP64 partial sums
   double* red_out = nullptr;   // FP64 results (4)
   int red_blocks = 1024;

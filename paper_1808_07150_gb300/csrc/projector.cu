@@ -194,147 +194,230 @@ __device__ __forceinline__ int row_entries(const DevGeom& g, const Line& L, bool
   return n;
 }
 
-template <int NT, int PPT, int MODE>
-__global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int rpc, int split, int xs_stride,
-                                                 FwdArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int warp_tot[2];
-  __shared__ int n_ent_sh;
-  const int cap = kCandPerRow * rpc;
-  float* xs = reinterpret_cast<float*>(smem);      // staged x columns: [entry][xs_stride]
-  Entry* ent = reinterpret_cast<Entry*>(xs + (size_t)cap * xs_stride);
-  int* tapJ = reinterpret_cast<int*>(ent + cap);   // j0 | (nt << 24) per (segment, entry)
-  float* tapL = reinterpret_cast<float*>(tapJ + g.n_seg * cap);
-  const int nimg = g.nx * g.ny * g.nz;
+constexpr int kFwdChunk = 32;  // pixel entries per double-buffered chunk
 
-  // block = (line, part): `split` blocks share the planes of one LOR line
+// Block-wide exclusive prefix sum of one int per thread (blockDim <= 1024); returns the
+// exclusive prefix and writes the total to *total.  Uses `scratch` (>= 33 ints of shared).
+__device__ __forceinline__ int block_exclusive_scan(int v, int* scratch, int* total) {
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) scratch[wi] = incl;
+  __syncthreads();
+  if (wi == 0) {
+    int t = lane < nw ? scratch[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < nw) scratch[lane] = t;  // inclusive warp totals
+    if (lane == 31) scratch[32] = t;
+  }
+  __syncthreads();
+  const int excl = incl - v + (wi > 0 ? scratch[wi - 1] : 0);
+  *total = scratch[32];
+  __syncthreads();
+  return excl;
+}
+
+// Forward projection.  A block owns the rows [row_lo, row_hi) of one transaxial LOR line
+// (view, radial bin) and all its planes.  All threads first find the pixels the line crosses in
+// those rows (exact intervals, compacted); the entries are then processed in chunks of
+// kFwdChunk: the x columns of chunk c+1 are copied to shared memory (cp.async, with NT-1 zeros
+// on each side so that taps leaving the image read zeros) and its axial taps computed while
+// chunk c is accumulated, one thread per plane.  When several blocks share a line, each writes
+// partial plane sums and the last one to finish reduces them in a fixed order.
+template <int NT, int PPT, int MODE>
+__global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap, int split, int xs_stride,
+                                                 FwdArgs a, float* part_acc, float* part_chord,
+                                                 unsigned* tickets) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int scan_scratch[33];
+  constexpr int PAD = NT - 1;
+  float* xs = reinterpret_cast<float*>(smem);                             // [2][kFwdChunk][xs_stride]
+  float4* tapL = reinterpret_cast<float4*>(xs + 2 * kFwdChunk * xs_stride);  // [2][n_seg][kFwdChunk]
+  int4* tapM = reinterpret_cast<int4*>(tapL + 2 * g.n_seg * kFwdChunk);      // [2][n_seg][kFwdChunk]
+  Entry* ent = reinterpret_cast<Entry*>(tapM + 2 * g.n_seg * kFwdChunk);     // [ecap]
+  const int nz = g.nz;
+
   const int line = blockIdx.x / split, part = blockIdx.x - line * split;
   const int l = line / g.R, r = line - (line / g.R) * g.R;
   const int v = subset_view(g, subset, l);
   const Line L = make_line(g, v, r);
-  const int per_part = (g.P + split - 1) / split;
-  const int p_lo = part * per_part, p_hi = min(g.P, p_lo + per_part);
-  const int g_lo = g.plane_seg[min(p_lo, g.P - 1)], g_hi = g.plane_seg[max(p_hi - 1, 0)];
 
-  int pseg[PPT], pq[PPT];
+  // planes of this thread: lane of warp-sized runs of one segment (run = warp + k * nwarps)
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  int pseg[PPT], pq[PPT], pp[PPT];
+  bool pvalid[PPT];
   float acc[PPT], chord[PPT];
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    const int p = p_lo + threadIdx.x + k * blockDim.x;
+    const int run = wi + k * nwarps;
     acc[k] = 0.f;
     chord[k] = 0.f;
-    if (p < p_hi) {
-      const int gi = g.plane_seg[p];
-      pseg[k] = gi;
-      pq[k] = p - g.seg[gi].p0;
-    } else {
-      pseg[k] = -1;
-      pq[k] = 0;
+    pseg[k] = -1;
+    pq[k] = 0;
+    pp[k] = 0;
+    pvalid[k] = false;
+    if (run < g.n_runs) {
+      const int2 ru = g.runs[run];
+      const SegDev sd = g.seg[ru.x];
+      pseg[k] = ru.x;
+      pq[k] = ru.y + lane;
+      pp[k] = sd.p0 + pq[k];
+      pvalid[k] = pq[k] < sd.n;
     }
   }
+  // zero pads of the staged columns (never overwritten by the copies)
+  for (int i = threadIdx.x; i < 2 * kFwdChunk * 2 * PAD; i += blockDim.x) {
+    const int col = i / (2 * PAD), k = i - col * (2 * PAD);
+    xs[col * xs_stride + (k < PAD ? k : nz + k)] = 0.f;
+  }
   const bool ydom = fabsf(L.c_hi) >= fabsf(L.s_hi);  // |dy| >= |dx|: walk the rows of y
-  const int nrows = ydom ? g.ny : g.nx;
-  const int nz = g.nz;
-  const int nseg_part = g_hi - g_lo + 1;
+  const int nrows_all = ydom ? g.ny : g.nx;
+  const int rows_per_part = (nrows_all + split - 1) / split;
+  const int row_lo = part * rows_per_part, row_hi = min(nrows_all, row_lo + rows_per_part);
 
-  for (int row0 = 0; row0 < nrows; row0 += rpc) {
-    // 1. rows -> exact pixel intervals, compacted with a two-warp prefix sum (rpc <= 64)
+  // A. this block's rows -> exact pixel intervals, compacted into ent[]
+  int n_ent = 0;
+  for (int row0 = row_lo; row0 < row_hi; row0 += blockDim.x) {
     Entry loc[kCandPerRow];
-    int cnt = 0;
-    if (threadIdx.x < rpc && row0 + (int)threadIdx.x < nrows) cnt = row_entries(g, L, ydom, row0 + threadIdx.x, loc);
-    int incl = 0;
-    if (threadIdx.x < 64) {
-      const int lane = threadIdx.x & 31;
-      incl = cnt;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      if (lane == 31) warp_tot[threadIdx.x >> 5] = incl;
+    const int row = row0 + threadIdx.x;
+    const int cnt = row < row_hi ? row_entries(g, L, ydom, row, loc) : 0;
+    int total;
+    const int off = n_ent + block_exclusive_scan(cnt, scan_scratch, &total);
+    for (int k = 0; k < cnt; ++k)
+      if (off + k < ecap) ent[off + k] = loc[k];
+    n_ent = min(n_ent + total, ecap);
+  }
+  __syncthreads();
+
+  auto stage = [&](int c) {  // x columns + taps of chunk c into buffer c & 1
+    const int buf = c & 1;
+    const int e0 = c * kFwdChunk, ne = min(kFwdChunk, n_ent - e0);
+    float* xb = xs + buf * kFwdChunk * xs_stride;
+    for (int i = threadIdx.x; i < ne * nz; i += blockDim.x) {
+      const int e = i / nz, iz = i - e * nz;
+      cp_async4(xb + e * xs_stride + PAD + iz, a.x + ent[e0 + e].col * nz + iz);
     }
-    __syncthreads();
-    if (threadIdx.x < 64) {
-      const int off = incl - cnt + (threadIdx.x >= 32 ? warp_tot[0] : 0);
-      for (int k = 0; k < cnt; ++k) ent[off + k] = loc[k];
-      if (threadIdx.x == 0) n_ent_sh = warp_tot[0] + (rpc > 32 ? warp_tot[1] : 0);
-    }
-    __syncthreads();
-    const int n_ent = n_ent_sh;
-    // 1b. stage the x columns of the entries (16-byte copies of the aligned cover of each
-    //     column; 4-byte copies at the end of the image), overlapped with the taps below
-    {
-      const int chunks = xs_stride / 4;
-      for (int i = threadIdx.x; i < n_ent * chunks; i += blockDim.x) {
-        const int e = i / chunks, k = i - e * chunks;
-        const int gbase = (ent[e].col * nz) & ~3;
-        const int gi0 = gbase + 4 * k;
-        float* dst = xs + e * xs_stride + 4 * k;
-        if (gi0 + 4 <= nimg) {
-          cp_async16(dst, a.x + gi0);
-        } else {
-          for (int q = 0; q < 4; ++q)
-            if (gi0 + q < nimg) cp_async4(dst + q, a.x + gi0 + q);
-        }
-      }
-    }
-    // 2. axial taps of every (entry, segment of this block's planes)
-    for (int it = threadIdx.x; it < nseg_part * n_ent; it += blockDim.x) {
-      const int gi = g_lo + it / n_ent, e = it - (it / n_ent) * n_ent;
-      float Lk[NT];
-      const int j0 = segment_taps<NT>(g, r, gi, ent[e].I, Lk);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    float4* tl = tapL + buf * g.n_seg * kFwdChunk;
+    int4* tm = tapM + buf * g.n_seg * kFwdChunk;
+    for (int it = threadIdx.x; it < g.n_seg * ne; it += blockDim.x) {
+      const int gs = it / ne, e = it - gs * ne;
+      float Lk[4] = {0.f, 0.f, 0.f, 0.f};
+      const int j0 = segment_taps<NT>(g, r, gs, ent[e0 + e].I, Lk);
       int nt = NT;
       while (nt > 1 && Lk[nt - 1] == 0.f) --nt;
-      const int slot = gi * cap + e;
-      tapJ[slot] = (j0 & 0xffffff) | (nt << 24);
-#pragma unroll
-      for (int k = 0; k < NT; ++k) tapL[slot * NT + k] = Lk[k];
+      const int slot = gs * kFwdChunk + e;
+      tl[slot] = make_float4(Lk[0], Lk[1], Lk[2], Lk[3]);
+      // plane q, tap t reads xs[e * stride + PAD + q - j0 - t]; useful while 0 <= q - j0 < nz + PAD
+      tm[slot] = make_int4(e * xs_stride + PAD - j0, j0, nt, 0);
     }
-    cp_async_commit_wait_all();
+  };
+
+  const int nchunks = (n_ent + kFwdChunk - 1) / kFwdChunk;
+  if (nchunks > 0) stage(0);
+  for (int c = 0; c < nchunks; ++c) {
+    if (c + 1 < nchunks) {
+      stage(c + 1);
+      asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    }
     __syncthreads();
-    // 3. accumulate the planes of this thread over the entries
-    for (int e = 0; e < n_ent; ++e) {
-      const float* xc = xs + e * xs_stride + ((ent[e].col * nz) & 3);
+    const int buf = c & 1;
+    const int ne = min(kFwdChunk, n_ent - c * kFwdChunk);
+    const float* xb = xs + buf * kFwdChunk * xs_stride;
+    const float4* tl = tapL + buf * g.n_seg * kFwdChunk;
+    const int4* tm = tapM + buf * g.n_seg * kFwdChunk;
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        if (pseg[k] < 0) continue;
-        const int slot = pseg[k] * cap + e;
-        const int jn = tapJ[slot];
-        const int nt = jn >> 24;
-        const int iz = pq[k] - ((jn << 8) >> 8);  // sign-extended j0
-#pragma unroll
-        for (int t = 0; t < NT; ++t) {
-          if (t < nt) {
-            const float Lt = tapL[slot * NT + t];
-            const int izt = iz - t;
-            if ((unsigned)izt < (unsigned)nz) {
-              acc[k] = fmaf(Lt, xc[izt], acc[k]);
-              if (MODE != FWD_PROJECT) chord[k] += Lt;
-            }
-          }
+    for (int k = 0; k < PPT; ++k) {
+      if (pseg[k] < 0) break;  // warp-uniform: no more runs for this warp
+      const float4* tlk = tl + pseg[k] * kFwdChunk;
+      const int4* tmk = tm + pseg[k] * kFwdChunk;
+      const int q = pq[k];
+      float sum = 0.f;
+      for (int e = 0; e < ne; ++e) {
+        const int4 M = tmk[e];     // warp broadcast: one segment per warp
+        const float4 Lv = tlk[e];
+        const int d = q - M.y;
+        const bool in = (unsigned)d < (unsigned)(nz + PAD);
+        const float* xp = xb + M.x + q;  // taps t read xp[-t], inside the zero-padded column
+        if (MODE == FWD_SIGMA) {  // chord of the LOR inside the image: taps whose slab exists
+          if (in)
+            chord[k] += (d < nz ? Lv.x : 0.f) + (NT > 1 && d >= 1 && d - 1 < nz ? Lv.y : 0.f) +
+                        (NT > 2 && d >= 2 && d - 2 < nz ? Lv.z : 0.f) + (NT > 3 && d >= 3 && d - 3 < nz ? Lv.w : 0.f);
+        } else if (NT == 1 || M.z == 1) {  // tap count is uniform across the warp
+          if (in) sum = fmaf(Lv.x, xp[0], sum);
+        } else if (NT == 2 || M.z == 2) {
+          if (in) sum = fmaf(Lv.y, xp[-1], fmaf(Lv.x, xp[0], sum));
+        } else if (NT == 3 || M.z == 3) {
+          if (in) sum = fmaf(Lv.z, xp[-2], fmaf(Lv.y, xp[-1], fmaf(Lv.x, xp[0], sum)));
+        } else {
+          if (in) sum = fmaf(Lv.w, xp[-3], fmaf(Lv.z, xp[-2], fmaf(Lv.y, xp[-1], fmaf(Lv.x, xp[0], sum))));
         }
       }
+      acc[k] += sum;
     }
     __syncthreads();
+  }
+
+  if (split > 1) {
+    // publish this block's partial sums; the last block of the line reduces them
+    __shared__ unsigned last_sh;
+    const size_t pbase = ((size_t)line * split + part) * g.P;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      if (!pvalid[k]) continue;
+      const int p = pp[k];
+      part_acc[pbase + p] = acc[k];
+      if (MODE == FWD_SIGMA) part_chord[pbase + p] = chord[k];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last_sh = (atomicAdd(tickets + line, 1u) == (unsigned)split - 1u) ? 1u : 0u;
+    __syncthreads();
+    if (!last_sh) return;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      if (!pvalid[k]) continue;
+      const int p = pp[k];
+      float sa = 0.f, sc = 0.f;
+      for (int q = 0; q < split; ++q) {  // fixed order: deterministic
+        const size_t o = ((size_t)line * split + q) * g.P + p;
+        sa += __ldcg(part_acc + o);
+        if (MODE == FWD_SIGMA) sc += __ldcg(part_chord + o);
+      }
+      acc[k] = sa;
+      chord[k] = sc;
+    }
+    if (threadIdx.x == 0) tickets[line] = 0u;  // ready for the next launch
   }
 
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    const int p = p_lo + threadIdx.x + k * blockDim.x;
-    if (p >= p_hi) continue;
+    if (!pvalid[k]) continue;
+    const int p = pp[k];
     const size_t j = ((size_t)v * g.R + r) * g.P + p;
     const float mu = a.mult ? a.mult[j] : 1.f;
     if (MODE == FWD_PROJECT) {
       a.out[j] = mu * acc[k];
     } else if (MODE == FWD_SIGMA) {
+      // sigma_j = gamma rho / (P_i 1)_j,  (P_i 1)_j = mult_j * chord_j  (Eq. EQU:STEPSIZE:PRECOND)
       const float a1 = mu * chord[k];
       a.out[j] = a1 > 0.f ? a.gamma_rho / a1 : 0.f;
     } else {
       // KL dual prox on this bin:  y+ = prox_{sigma varphi*}(y + sigma (P_i x)_j), evaluated as
       // 2 (w - sigma b) / (w + 1 + sqrt((w - 1)^2 + 4 sigma b)),  w = y + sigma ((P_i x)_j + r_j),
       // which equals 1/2 [w + 1 - sqrt((w - 1)^2 + 4 sigma b)] without its cancellation.
-      const float a1 = mu * chord[k];
-      const float sigma = a1 > 0.f ? a.gamma_rho / a1 : 0.f;
+      const float sigma = a.sigma[j];
       const float yj = a.y[j];
       const float bj = a.b[j];
       const float w = fmaf(sigma, fmaf(mu, acc[k], a.r[j]), yj);
@@ -363,17 +446,22 @@ constexpr int kBwdMaxItems = 64;         // (pair, segment) items per column and
 
 // Backprojection.  A block owns a 4 x 4 tile of voxel columns; for each view of the subset it
 // stages the contiguous radial rows w[view][r_min..r_max][0..P) that the tile's footprints
-// touch into shared memory (cp.async, overlapped with the geometry below).  Each warp owns one
+// touch into shared memory (cp.async, overlapped with the geometry below), each segment's plane
+// run framed by NT-1 zeros so that taps leaving the segment read zeros.  Each warp owns one
 // column: its lanes find the footprint (bin, pixel interval) pairs, compact them with a ballot,
-// compute the axial taps of every (pair, segment) item, and then gather along contiguous
-// plane runs from shared memory, lane = iz mod 32, ZK voxels per lane.
+// compute the axial taps of every (pair, segment) item, and then gather along contiguous plane
+// runs from shared memory, lane = iz mod 32, ZK voxels per lane.
 template <int NT, int ZK, int MODE>
-__global__ void __launch_bounds__(kBwdWarps * 32) k_backward(DevGeom g, int subset, int nr_tile, BwdArgs a) {
+__global__ void __launch_bounds__(kBwdWarps * 32) k_backward(DevGeom g, int subset, int nr_tile, int p_pad,
+                                                             int bcap, BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float* sw = reinterpret_cast<float*>(smem);                                  // nr_tile x P
-  float4* itL = reinterpret_cast<float4*>(sw + ((nr_tile * g.P + 3) & ~3));    // [warp][item]
-  int4* itM = reinterpret_cast<int4*>(itL + kBwdWarps * kBwdMaxItems);
-  PixItem* pix = reinterpret_cast<PixItem*>(itM + kBwdWarps * kBwdMaxItems);  // [warp][32]
+  constexpr int PAD = NT - 1;
+  const int icap = NT * bcap;  // items per warp: NT buckets of bcap
+  float* sw = reinterpret_cast<float*>(smem);                                  // nr_tile x p_pad
+  float4* itL = reinterpret_cast<float4*>(sw + ((nr_tile * p_pad + 3) & ~3));  // [warp][icap]
+  int4* itM = reinterpret_cast<int4*>(itL + kBwdWarps * icap);
+  PixItem* pix = reinterpret_cast<PixItem*>(itM + kBwdWarps * icap);          // [warp][nr_max]
+  int* seg_of = reinterpret_cast<int*>(pix + kBwdWarps * g.nr_max);           // [P]: padded position
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const int tx0 = blockIdx.x * kBwdTile, ty0 = blockIdx.y * kBwdTile;
   const int ix = tx0 + (wi % kBwdTile), iy = ty0 + (wi / kBwdTile);
@@ -382,14 +470,24 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_backward(DevGeom g, int subs
   const float Yc = (float)iy + 0.5f - 0.5f * (float)g.ny;
   const float X0 = (float)tx0 + 0.5f - 0.5f * (float)g.nx, Y0 = (float)ty0 + 0.5f - 0.5f * (float)g.ny;
   const float X1 = X0 + (float)(kBwdTile - 1), Y1 = Y0 + (float)(kBwdTile - 1);
-  float4* myL = itL + wi * kBwdMaxItems;
-  int4* myM = itM + wi * kBwdMaxItems;
-  PixItem* mypix = pix + wi * 32;
+  float4* myL = itL + wi * icap;
+  int4* myM = itM + wi * icap;
+  PixItem* mypix = pix + wi * g.nr_max;
   const int nviews = subset_views(g, subset);
   const int nz = g.nz;
   float acc[ZK];
 #pragma unroll
   for (int k = 0; k < ZK; ++k) acc[k] = 0.f;
+  // padded position of every plane, and the zero frames of the staged rows (written once)
+  for (int p = threadIdx.x; p < g.P; p += blockDim.x) seg_of[p] = p + (2 * g.plane_seg[p] + 1) * PAD;
+  for (int i = threadIdx.x; i < nr_tile * g.n_seg * 2 * PAD; i += blockDim.x) {
+    const int rr = i / (g.n_seg * 2 * PAD), rem = i - rr * (g.n_seg * 2 * PAD);
+    const int gi = rem / (2 * PAD), k = rem - gi * (2 * PAD);
+    const SegDev sd = g.seg[gi];
+    const int start = sd.p0 + 2 * gi * PAD;  // first slot of the segment's frame
+    sw[rr * p_pad + (k < PAD ? start + k : start + PAD + sd.n + (k - PAD))] = 0.f;
+  }
+  __syncthreads();
 
   for (int l = 0; l < nviews; ++l) {
     const int v = subset_view(g, subset, l);
@@ -401,11 +499,14 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_backward(DevGeom g, int subs
     const float smin = fminf(fminf(s00, s01), fminf(s10, s11)), smax = fmaxf(fmaxf(s00, s01), fmaxf(s10, s11));
     const int r_min = max(0, (int)ceilf((smin - hw) * g.inv_drp + g.half_R) - 1);
     const int r_max = min(g.R - 1, min(r_min + nr_tile - 1, (int)floorf((smax + hw) * g.inv_drp + g.half_R) + 1));
-    // 1. stage rows r_min..r_max of this view (contiguous)
+    // 1. stage rows r_min..r_max of this view into their padded slots
     {
       const float* src = a.w + ((size_t)l * g.R + r_min) * g.P;
       const int n = (r_max - r_min + 1) * g.P;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) cp_async4(sw + i, src + i);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int rr = i / g.P, p = i - rr * g.P;
+        cp_async4(sw + rr * p_pad + seg_of[p], src + i);
+      }
     }
     // 2. footprint pairs of this warp's column (overlaps the copy)
     PixItem P;
@@ -426,36 +527,60 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_backward(DevGeom g, int subs
     if (ok) mypix[__popc(mask & ((1u << lane) - 1u))] = P;
     const int np = __popc(mask);
     __syncwarp();
-    // 3. axial taps per (pair, segment)
-    const int ni = min(np * g.n_seg, kBwdMaxItems);
-    for (int it = lane; it < ni; it += 32) {
-      const int pi = it / g.n_seg, gi = it - pi * g.n_seg;
-      const PixItem Q = mypix[pi];
-      float Lk[NT];
-      const int j0 = segment_taps<NT>(g, Q.r, gi, Q.I, Lk);
-      int nt = NT;
-      while (nt > 1 && Lk[nt - 1] == 0.f) --nt;
-      const SegDev sd = g.seg[gi];
-      float4 Lv = make_float4(Lk[0], NT > 1 ? Lk[1] : 0.f, NT > 2 ? Lk[2] : 0.f, NT > 3 ? Lk[3] : 0.f);
-      myL[it] = Lv;
-      // smem index of (iz, tap t): a + iz + t, valid while lo <= iz + t < hi
-      myM[it] = make_int4((Q.r - r_min) * g.P + sd.p0 + j0, -j0, sd.n - j0, nt);
+    // 3. axial taps per (pair, segment), bucketed by tap count (ballot compaction per bucket)
+    const int ni = min(np * g.n_seg, bcap);
+    int nb[4] = {0, 0, 0, 0};  // items with 1, 2, 3, 4 taps
+    for (int it0 = 0; it0 < ni; it0 += 32) {
+      const int it = it0 + lane;
+      float4 Lv = make_float4(0.f, 0.f, 0.f, 0.f);
+      int4 Mv = make_int4(0, 0, 0, 1);
+      int nt = 0;
+      if (it < ni) {
+        const int pi = it / g.n_seg, gi = it - pi * g.n_seg;
+        const PixItem Q = mypix[pi];
+        float Lk[4] = {0.f, 0.f, 0.f, 0.f};
+        const int j0 = segment_taps<NT>(g, Q.r, gi, Q.I, Lk);
+        nt = NT;
+        while (nt > 1 && Lk[nt - 1] == 0.f) --nt;
+        const SegDev sd = g.seg[gi];
+        Lv = make_float4(Lk[0], Lk[1], Lk[2], Lk[3]);
+        // voxel iz, tap t reads plane q = iz + j0 + t at sw[x + iz + t]; some tap is inside the
+        // segment while -PAD <= iz + j0 < n, and the frame supplies zeros for the others
+        Mv = make_int4((Q.r - r_min) * p_pad + sd.p0 + (2 * gi + 1) * PAD + j0, j0 + PAD, sd.n + PAD, nt);
+      }
+#pragma unroll
+      for (int b = 0; b < NT; ++b) {
+        const unsigned m = __ballot_sync(0xffffffffu, nt == b + 1);
+        if (nt == b + 1) {
+          const int slot = b * bcap + nb[b] + __popc(m & ((1u << lane) - 1u));
+          myL[slot] = Lv;
+          myM[slot] = Mv;
+        }
+        nb[b] += __popc(m);
+      }
     }
     cp_async_commit_wait_all();
     __syncthreads();
-    // 4. gather
+    // 4. gather: one branch-free loop per tap count
     if (live) {
-      for (int it = 0; it < ni; ++it) {
-        const float4 Lv = myL[it];
-        const int4 M = myM[it];
-        const float Lt[4] = {Lv.x, Lv.y, Lv.z, Lv.w};
-        const unsigned span = (unsigned)(M.z - M.y);
 #pragma unroll
-        for (int k = 0; k < ZK; ++k) {
-          const int iz = lane + 32 * k;
+      for (int b = 0; b < NT; ++b) {
+        const int base = b * bcap;
+        for (int it = base; it < base + nb[b]; ++it) {
+          const float4 Lv = myL[it];
+          const int4 M = myM[it];
+          const float* src0 = sw + M.x;
 #pragma unroll
-          for (int t = 0; t < NT; ++t) {
-            if (t < M.w && (unsigned)(iz + t - M.y) < span) acc[k] = fmaf(Lt[t], sw[M.x + iz + t], acc[k]);
+          for (int k = 0; k < ZK; ++k) {
+            const int iz = lane + 32 * k;
+            if ((unsigned)(iz + M.y) < (unsigned)M.z) {
+              const float* src = src0 + iz;
+              float sum = Lv.x * src[0];
+              if (b >= 1) sum = fmaf(Lv.y, src[1], sum);
+              if (b >= 2) sum = fmaf(Lv.z, src[2], sum);
+              if (b >= 3) sum = fmaf(Lv.w, src[3], sum);
+              acc[k] += sum;
+            }
           }
         }
       }
@@ -497,48 +622,45 @@ __global__ void k_gather_subset(DevGeom g, int subset, const float* __restrict__
 // launchers
 // ---------------------------------------------------------------------------------------
 
-static int fwd_split(const DevGeom& g) {
+int forward_split(const DevGeom& g, int subset) {
   if (g.tune[SPDHG_TUNE_FWD_SPLIT]) return g.tune[SPDHG_TUNE_FWD_SPLIT];
-  return 1;
-}
-
-static int fwd_threads(int planes, int* ppt) {
-  int t = (planes + 2) / 3;
-  t = ((t + 31) / 32) * 32;
-  t = t < 128 ? 128 : (t > 512 ? 512 : t);
-  int k = (planes + t - 1) / t;
-  *ppt = k < 1 ? 1 : k;
-  return t;
+  // enough blocks for every SM: one LOR line per block is too few for small subsets
+  const int lines = subset_views(g, subset) * g.R;
+  const int nrows = g.nx > g.ny ? g.nx : g.ny;
+  int split = 1;
+  while (split < 8 && lines * split < 152 && nrows / (split * 2) >= 32) split *= 2;
+  return split;
 }
 
 template <int NT, int PPT, int MODE>
 static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cudaStream_t s, int threads, int split) {
-  // x column of nz floats staged as the 16-byte aligned cover: ceil((nz + 3) / 4) * 4 floats
-  const int xs_stride = ((g.nz + 3 + 3) / 4) * 4;
-  auto bytes = [&](int rows) {
-    const size_t cap = (size_t)kCandPerRow * rows;
-    return cap * ((size_t)xs_stride * sizeof(float) + sizeof(Entry) + (size_t)g.n_seg * sizeof(int) +
-                  (size_t)g.n_seg * NT * sizeof(float));
-  };
-  int rpc = 64;
-  while (rpc > 8 && bytes(rpc) > 72 * 1024) rpc /= 2;
-  const size_t smem = bytes(rpc);
+  const int xs_stride = g.nz + 2 * (NT - 1);  // staged x column with zero pads
+  const int nrows = g.nx > g.ny ? g.nx : g.ny;
+  const int ecap = 3 * nrows + 8;  // a line crosses at most two pixels per row of its dominant axis
+  const size_t smem = (size_t)2 * kFwdChunk * xs_stride * sizeof(float) +
+                      (size_t)2 * g.n_seg * kFwdChunk * (sizeof(float4) + sizeof(int4)) + (size_t)ecap * sizeof(Entry);
+  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (MODE == FWD_DATA && !a.sigma) return cudaErrorInvalidValue;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_forward<NT, PPT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   const int lines = subset_views(g, subset) * g.R;
   if (lines == 0) return cudaSuccess;
-  k_forward<NT, PPT, MODE><<<lines * split, threads, smem, s>>>(g, subset, rpc, split, xs_stride, a);
+  if (split > 1 && (!a.part_acc || !a.part_chord || !a.tickets || (size_t)lines * split * g.P > a.part_cap ||
+                    (size_t)lines > a.ticket_cap))
+    return cudaErrorInvalidValue;
+  k_forward<NT, PPT, MODE><<<lines * split, threads, smem, s>>>(g, subset, ecap, split, xs_stride, a, a.part_acc,
+                                                                a.part_chord, a.tickets);
   return cudaGetLastError();
 }
 
 template <int NT, int MODE>
 static cudaError_t fwd_ppt(const DevGeom& g, int subset, const FwdArgs& a, cudaStream_t s) {
-  int split = fwd_split(g);
-  if (split > g.P) split = g.P;
-  int ppt;
-  const int threads = fwd_threads((g.P + split - 1) / split, &ppt);
+  const int split = forward_split(g, subset);
+  const int nwarps = g.n_runs < 16 ? (g.n_runs < 4 ? 4 : g.n_runs) : 16;  // >= 128 threads
+  const int ppt = (g.n_runs + nwarps - 1) / nwarps;                      // runs per warp
+  const int threads = nwarps * 32;
   switch (ppt) {
     case 1: return fwd_launch<NT, 1, MODE>(g, subset, a, s, threads, split);
     case 2: return fwd_launch<NT, 2, MODE>(g, subset, a, s, threads, split);
@@ -577,11 +699,14 @@ template <int NT, int ZK, int MODE>
 static cudaError_t bwd_launch(const DevGeom& g, int subset, const BwdArgs& a, cudaStream_t s) {
   // at most floor(sqrt(2) vx / d_radial) + 2 bins of one view cross a pixel
   const int max_pairs = (int)floorf(1.4143f * g.inv_drp) + 2;
-  if (g.nr_max > 32 || max_pairs * g.n_seg > kBwdMaxItems) return cudaErrorInvalidValue;
+  // items are bucketed by tap count: NT buckets of bcap items per warp
+  const int bcap = max_pairs * g.n_seg;
+  if (g.nr_max > 32 || bcap > kBwdMaxItems) return cudaErrorInvalidValue;
   const int nr_tile = bwd_rows_per_tile(g);
-  const size_t sw_floats = ((size_t)nr_tile * g.P + 3) & ~(size_t)3;
-  const size_t smem = sw_floats * sizeof(float) + (size_t)kBwdWarps * kBwdMaxItems * (sizeof(float4) + sizeof(int4)) +
-                      (size_t)kBwdWarps * 32 * sizeof(PixItem);
+  const int p_pad = g.P + 2 * (NT - 1) * g.n_seg;  // each segment framed by NT-1 zeros
+  const size_t sw_floats = ((size_t)nr_tile * p_pad + 3) & ~(size_t)3;
+  const size_t smem = sw_floats * sizeof(float) + (size_t)kBwdWarps * NT * bcap * (sizeof(float4) + sizeof(int4)) +
+                      (size_t)kBwdWarps * g.nr_max * sizeof(PixItem) + (size_t)g.P * sizeof(int);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   auto kern = k_backward<NT, ZK, MODE>;
   if (smem > 48 * 1024) {
@@ -589,7 +714,7 @@ static cudaError_t bwd_launch(const DevGeom& g, int subset, const BwdArgs& a, cu
     if (e != cudaSuccess) return e;
   }
   dim3 grid((g.nx + kBwdTile - 1) / kBwdTile, (g.ny + kBwdTile - 1) / kBwdTile);
-  kern<<<grid, kBwdWarps * 32, smem, s>>>(g, subset, nr_tile, a);
+  kern<<<grid, kBwdWarps * 32, smem, s>>>(g, subset, nr_tile, p_pad, bcap, a);
   return cudaGetLastError();
 }
 
