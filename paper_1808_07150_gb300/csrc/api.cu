@@ -245,6 +245,7 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   };
   const int R = g.n_radial, V = g.n_views, S = g.n_segments;
   std::vector<float4> view(V), rad(R), rs((size_t)R * S);
+  std::vector<float2> view_inv(V);
   for (int v = 0; v < V; ++v) {
     double c = cos(pi * v / V), sn = sin(pi * v / V);
     if (fabs(c) < 1e-12) c = 0.0;
@@ -253,6 +254,8 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
     split(c, t.x, t.y);
     split(sn, t.z, t.w);
     view[v] = t;
+    // reciprocals of the FP32 direction components, rounded once on the host
+    view_inv[v] = make_float2(t.z != 0.f ? (float)(1.0 / -(double)t.z) : 0.f, t.x != 0.f ? (float)(1.0 / (double)t.x) : 0.f);
   }
   for (int r = 0; r < R; ++r) {
     const double s = (r - 0.5 * (R - 1)) * g.d_radial;
@@ -300,6 +303,8 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   if ((e = cudaMemcpy(ctx->d_seg, seg.data(), sizeof(SegDev) * S, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_plane_seg, plane_seg.data(), sizeof(int) * P, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMalloc(&ctx->d_runs, sizeof(int2) * runs.size())) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMalloc(&ctx->d_view_inv, sizeof(float2) * V)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMemcpy(ctx->d_view_inv, view_inv.data(), sizeof(float2) * V, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_runs, runs.data(), sizeof(int2) * runs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
 
   DevGeom& d = ctx->dg;
@@ -316,6 +321,7 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   d.half_R = (float)(0.5 * (R - 1));
   d.inv_drp = (float)(g.vx / g.d_radial);
   d.view = ctx->d_view;
+  d.view_inv = ctx->d_view_inv;
   d.rad = ctx->d_rad;
   d.rs = ctx->d_rs;
   d.seg = ctx->d_seg;
@@ -328,7 +334,7 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
 
 void spdhg_destroy(spdhg_ctx* ctx) {
   if (!ctx) return;
-  void* ptrs[] = {ctx->d_view, ctx->d_rad, ctx->d_rs, ctx->d_runs, ctx->d_seg, ctx->d_plane_seg, ctx->b, ctx->r, ctx->mult, ctx->side,
+  void* ptrs[] = {ctx->d_view, ctx->d_view_inv, ctx->d_rad, ctx->d_rs, ctx->d_runs, ctx->d_seg, ctx->d_plane_seg, ctx->b, ctx->r, ctx->mult, ctx->side,
                   ctx->x[0], ctx->x[1], ctx->z, ctx->T, ctx->y, ctx->sigma, ctx->wdy, ctx->q[0], ctx->q[1],
                   ctx->w[0], ctx->w[1], ctx->zw, ctx->q2[0], ctx->q2[1], ctx->tmp_sino, ctx->tmp_img, ctx->fwd_part, ctx->fwd_tickets,
                   ctx->red, ctx->red_out};

@@ -36,6 +36,7 @@ struct DevGeom {
   float half_R;          // (R - 1) / 2
   float inv_drp;         // vx / d_radial: radial bins per pixel unit
   const float4* view;    // per view: cos_hi, cos_lo, sin_hi, sin_lo (exact zeros on the axes)
+  const float2* view_inv;  // per view: 1 / (-sin_hi), 1 / cos_hi (0 where the component is 0)
   const float4* rad;     // per radial bin: s_hi, s_lo, h_hi, h_lo (s = signed offset, h = half chord)
   const float4* rs;      // per (radial bin, segment): kappa_hi, kappa_lo, len_scale, 0
   const SegDev* seg;
@@ -153,6 +154,7 @@ struct spdhg_ctx {
   float4* d_rad = nullptr;
   float4* d_rs = nullptr;
   int2* d_runs = nullptr;
+  float2* d_view_inv = nullptr;
   spdhg::SegDev* d_seg = nullptr;
   int* d_plane_seg = nullptr;
   // data

@@ -33,12 +33,14 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
 struct Line {
   float c_hi, c_lo, s_hi, s_lo;
   float sp_hi, sp_lo, h_hi, h_lo;
+  float inv_dx, inv_dy;  // 1 / (-s_hi), 1 / c_hi (0 for a zero component)
 };
 
 __device__ __forceinline__ Line make_line(const DevGeom& g, int v, int r) {
   const float4 a = g.view[v];
   const float4 b = g.rad[r];
-  return Line{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+  const float2 iv = g.view_inv[v];
+  return Line{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, iv.x, iv.y};
 }
 
 // Intersection of a line with pixel (ix, iy), expressed relative to the foot point of the
@@ -75,14 +77,14 @@ __device__ __forceinline__ bool pixel_interval(const DevGeom& g, const Line& L, 
   if (dx == 0.f) {
     if (!(ex >= -0.5f && ex < 0.5f)) return false;
   } else {
-    const float u1 = __fdiv_rn(__fsub_rn(-0.5f, ex), dx), u2 = __fdiv_rn(__fsub_rn(0.5f, ex), dx);
+    const float u1 = __fmul_rn(__fsub_rn(-0.5f, ex), L.inv_dx), u2 = __fmul_rn(__fsub_rn(0.5f, ex), L.inv_dx);
     lo = fmaxf(lo, fminf(u1, u2));
     hi = fminf(hi, fmaxf(u1, u2));
   }
   if (dy == 0.f) {
     if (!(ey >= -0.5f && ey < 0.5f)) return false;
   } else {
-    const float u1 = __fdiv_rn(__fsub_rn(-0.5f, ey), dy), u2 = __fdiv_rn(__fsub_rn(0.5f, ey), dy);
+    const float u1 = __fmul_rn(__fsub_rn(-0.5f, ey), L.inv_dy), u2 = __fmul_rn(__fsub_rn(0.5f, ey), L.inv_dy);
     lo = fmaxf(lo, fminf(u1, u2));
     hi = fminf(hi, fmaxf(u1, u2));
   }
@@ -452,11 +454,11 @@ constexpr int kBwdMaxItems = 64;         // (pair, segment) items per column and
 // compute the axial taps of every (pair, segment) item, and then gather along contiguous plane
 // runs from shared memory, lane = iz mod 32, ZK voxels per lane.
 template <int NT, int ZK, int MODE>
-__global__ void __launch_bounds__(kBwdWarps * 32) k_backward(DevGeom g, int subset, int nr_tile, int p_pad,
+__global__ void __launch_bounds__(kBwdWarps * 32, 3) k_backward(DevGeom g, int subset, int nr_tile, int p_pad,
                                                              int bcap, BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int PAD = NT - 1;
-  const int icap = NT * bcap;  // items per warp: NT buckets of bcap
+  const int icap = bcap;  // items per warp (all buckets)
   float* sw = reinterpret_cast<float*>(smem);                                  // nr_tile x p_pad
   float4* itL = reinterpret_cast<float4*>(sw + ((nr_tile * p_pad + 3) & ~3));  // [warp][icap]
   int4* itM = reinterpret_cast<int4*>(itL + kBwdWarps * icap);
@@ -502,10 +504,10 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_backward(DevGeom g, int subs
     // 1. stage rows r_min..r_max of this view into their padded slots
     {
       const float* src = a.w + ((size_t)l * g.R + r_min) * g.P;
-      const int n = (r_max - r_min + 1) * g.P;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int rr = i / g.P, p = i - rr * g.P;
-        cp_async4(sw + rr * p_pad + seg_of[p], src + i);
+      const int nr = r_max - r_min + 1;
+      for (int p = threadIdx.x; p < g.P; p += blockDim.x) {
+        const int dst = seg_of[p];
+        for (int rr = 0; rr < nr; ++rr) cp_async4(sw + rr * p_pad + dst, src + rr * g.P + p);
       }
     }
     // 2. footprint pairs of this warp's column (overlaps the copy)
@@ -527,37 +529,54 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_backward(DevGeom g, int subs
     if (ok) mypix[__popc(mask & ((1u << lane) - 1u))] = P;
     const int np = __popc(mask);
     __syncwarp();
-    // 3. axial taps per (pair, segment), bucketed by tap count (ballot compaction per bucket)
+    // 3. axial taps per (pair, segment), ordered by tap count: a lane holds up to two items,
+    //    ballots count each tap-count bucket, and the items are written bucket after bucket
     const int ni = min(np * g.n_seg, bcap);
-    int nb[4] = {0, 0, 0, 0};  // items with 1, 2, 3, 4 taps
-    for (int it0 = 0; it0 < ni; it0 += 32) {
-      const int it = it0 + lane;
-      float4 Lv = make_float4(0.f, 0.f, 0.f, 0.f);
-      int4 Mv = make_int4(0, 0, 0, 1);
-      int nt = 0;
+    float4 Lv2[2];
+    int4 Mv2[2];
+    int nt2[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int it = lane + 32 * h;
+      Lv2[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+      Mv2[h] = make_int4(0, 0, 0, 0);
       if (it < ni) {
         const int pi = it / g.n_seg, gi = it - pi * g.n_seg;
         const PixItem Q = mypix[pi];
         float Lk[4] = {0.f, 0.f, 0.f, 0.f};
         const int j0 = segment_taps<NT>(g, Q.r, gi, Q.I, Lk);
-        nt = NT;
+        int nt = NT;
         while (nt > 1 && Lk[nt - 1] == 0.f) --nt;
         const SegDev sd = g.seg[gi];
-        Lv = make_float4(Lk[0], Lk[1], Lk[2], Lk[3]);
+        Lv2[h] = make_float4(Lk[0], Lk[1], Lk[2], Lk[3]);
         // voxel iz, tap t reads plane q = iz + j0 + t at sw[x + iz + t]; some tap is inside the
         // segment while -PAD <= iz + j0 < n, and the frame supplies zeros for the others
-        Mv = make_int4((Q.r - r_min) * p_pad + sd.p0 + (2 * gi + 1) * PAD + j0, j0 + PAD, sd.n + PAD, nt);
+        Mv2[h] = make_int4((Q.r - r_min) * p_pad + sd.p0 + (2 * gi + 1) * PAD + j0, j0 + PAD, sd.n + PAD, nt);
+        nt2[h] = nt;
       }
+    }
+    int bs[5] = {0, 0, 0, 0, 0};  // bucket b (items with b + 1 taps) spans [bs[b], bs[b + 1])
+    {
+      int off = 0;
 #pragma unroll
       for (int b = 0; b < NT; ++b) {
-        const unsigned m = __ballot_sync(0xffffffffu, nt == b + 1);
-        if (nt == b + 1) {
-          const int slot = b * bcap + nb[b] + __popc(m & ((1u << lane) - 1u));
-          myL[slot] = Lv;
-          myM[slot] = Mv;
+        const unsigned m0 = __ballot_sync(0xffffffffu, nt2[0] == b + 1);
+        const unsigned m1 = __ballot_sync(0xffffffffu, nt2[1] == b + 1);
+        const unsigned below = (1u << lane) - 1u;
+        if (nt2[0] == b + 1) {
+          const int slot = off + __popc(m0 & below);
+          myL[slot] = Lv2[0];
+          myM[slot] = Mv2[0];
         }
-        nb[b] += __popc(m);
+        if (nt2[1] == b + 1) {
+          const int slot = off + __popc(m0) + __popc(m1 & below);
+          myL[slot] = Lv2[1];
+          myM[slot] = Mv2[1];
+        }
+        bs[b] = off;
+        off += __popc(m0) + __popc(m1);
       }
+      bs[NT] = off;
     }
     cp_async_commit_wait_all();
     __syncthreads();
@@ -565,8 +584,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_backward(DevGeom g, int subs
     if (live) {
 #pragma unroll
       for (int b = 0; b < NT; ++b) {
-        const int base = b * bcap;
-        for (int it = base; it < base + nb[b]; ++it) {
+        for (int it = bs[b]; it < bs[b + 1]; ++it) {
           const float4 Lv = myL[it];
           const int4 M = myM[it];
           const float* src0 = sw + M.x;
@@ -699,13 +717,13 @@ template <int NT, int ZK, int MODE>
 static cudaError_t bwd_launch(const DevGeom& g, int subset, const BwdArgs& a, cudaStream_t s) {
   // at most floor(sqrt(2) vx / d_radial) + 2 bins of one view cross a pixel
   const int max_pairs = (int)floorf(1.4143f * g.inv_drp) + 2;
-  // items are bucketed by tap count: NT buckets of bcap items per warp
+  // items per warp and view (two per lane at most)
   const int bcap = max_pairs * g.n_seg;
   if (g.nr_max > 32 || bcap > kBwdMaxItems) return cudaErrorInvalidValue;
   const int nr_tile = bwd_rows_per_tile(g);
   const int p_pad = g.P + 2 * (NT - 1) * g.n_seg;  // each segment framed by NT-1 zeros
   const size_t sw_floats = ((size_t)nr_tile * p_pad + 3) & ~(size_t)3;
-  const size_t smem = sw_floats * sizeof(float) + (size_t)kBwdWarps * NT * bcap * (sizeof(float4) + sizeof(int4)) +
+  const size_t smem = sw_floats * sizeof(float) + (size_t)kBwdWarps * bcap * (sizeof(float4) + sizeof(int4)) +
                       (size_t)kBwdWarps * g.nr_max * sizeof(PixItem) + (size_t)g.P * sizeof(int);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   auto kern = k_backward<NT, ZK, MODE>;
