@@ -149,7 +149,7 @@ enum { SPDHG_STATE_X = 0, SPDHG_STATE_Z = 1, SPDHG_STATE_T = 2, SPDHG_STATE_Y = 
        SPDHG_STATE_Q = 4, SPDHG_STATE_SIGMA = 5, SPDHG_STATE_W = 6, SPDHG_STATE_ZW = 7,
        SPDHG_STATE_Q2 = 8 };
 /* Copies a state array into dst (host or device per `where`): X, Z, T (N floats), Y, SIGMA
- * (M floats; SIGMA is computed on request), Q (3N: first prior dual, components x,y,z), and for
+ * (M floats; SIGMA as stored by spdhg_setup), Q (3N: first prior dual, components x,y,z), and for
  * TGV W (3N), ZW (3N), Q2 (6N: xx,yy,zz,xy,xz,yz). */
 int spdhg_get(spdhg_ctx* ctx, int what, void* dst, int where, void* stream);
 
