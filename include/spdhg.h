@@ -92,6 +92,8 @@ typedef struct {
   uint64_t seed;              /* sampler seed (spdhg_run) */
   int epochs;                 /* spdhg_run: number of epochs */
   int objective_every;        /* spdhg_run: evaluate Psi every k epochs (0: never) */
+  int graph;                  /* spdhg_run: 1 = every epoch is one CUDA graph launch (the path of
+                                 spdhg_run_batch); 0 = kernels launched one by one */
 } spdhg_params;
 
 typedef struct {
@@ -191,12 +193,33 @@ int spdhg_backproject_noalloc(spdhg_ctx* ctx, const float* y, float* x, int subs
 enum { SPDHG_TUNE_PRIOR_COLS = 0,   /* prior kernel: voxel columns per block, incl. one halo column */
        SPDHG_TUNE_PRIOR_YCHUNK = 1, /* prior kernel: rows marched per block */
        SPDHG_TUNE_FWD_SPLIT = 2,    /* forward kernel: blocks sharing the planes of one LOR line */
-       SPDHG_TUNE_BWD_COLS = 3,     /* backward kernel: voxel columns per block */
+       SPDHG_TUNE_FWD_WARPS = 3,    /* forward kernel: warps per block (4, 8 or 16) */
        SPDHG_TUNE_KNOBS = 8 };
 
 /* Sets one launch-shape knob of the context (value 0: default).  Out-of-range values are rejected
  * with SPDHG_ERR_ARG. */
 int spdhg_tune(spdhg_ctx* ctx, int knob, int value);
+
+/* Picks the launch-shape knobs of the context by measurement: for each knob in turn, every
+ * admissible value is timed (CUDA events on `stream`, `reps` launches after one warm-up) on the
+ * kernel it shapes, with the current state and data but scratch outputs (the reconstruction
+ * state is not changed), and the fastest value is kept.  Requires spdhg_setup.  chosen (NULL or
+ * SPDHG_TUNE_KNOBS ints) receives the resulting knob values (0 = built-in choice kept). */
+int spdhg_autotune(spdhg_ctx* ctx, int reps, int* chosen, void* stream);
+
+/* Many reconstructions, one CUDA graph launch per epoch (no counterpart in the paper, which
+ * reconstructs one data set at a time).  For each r < n: spdhg_setup(ctx[r], &params[r],
+ * x_inout[r]) as spdhg_run does, then params[r].epochs epochs.  Every epoch of all contexts is
+ * one graph: each context is an independent branch holding its iterations' kernels in order,
+ * with the block sequence of the epoch (spdhg_sample with params[r].seed, as spdhg_run) written
+ * into the branch before the launch; a context whose epochs are done idles.  Results are
+ * bit-identical to spdhg_run of each context alone.  Contexts must be distinct and on the
+ * current device; x_inout (NULL, or n pointers each NULL or N_r floats, host or device per
+ * `where`) receives the final iterates; reports (NULL or n) as in spdhg_run, with epoch_ms the
+ * device time of the whole batch epoch.  Errors are reported on the context concerned (the first
+ * one for graph-wide failures). */
+int spdhg_run_batch(spdhg_ctx* const* ctx, const spdhg_params* params, float* const* x_inout,
+                    int where, int n, spdhg_report* reports, void* stream);
 
 /* Kernel classes timed by the per-launch profiler. */
 enum { SPDHG_KERNEL_FORWARD = 0,   /* subset projection fused with the KL dual prox */

@@ -17,7 +17,7 @@ import numpy as np
 from . import _capi
 from ._capi import PRIOR, SAMPLING, STATE, SpdhgError, make_params  # noqa: F401
 
-__all__ = ["Context", "spdhg_sample", "make_params", "SpdhgError", "build", "library_path"]
+__all__ = ["Context", "spdhg_sample", "spdhg_run_batch", "make_params", "SpdhgError", "build", "library_path"]
 
 
 def build(force: bool = False) -> str:
@@ -141,18 +141,19 @@ class Context:
 
     def spdhg_run(self, params, x, stream=None):
         px = _capi.pointer(x, self.n_voxels)
-        obj = np.full(params.epochs + 1, np.nan)
-        ms = np.zeros(max(params.epochs, 1))
-        rep = _capi.Report(0, 0, obj.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                           ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        rep, keep = _report(params)
         self._check(_capi.lib().spdhg_run(self.h, ctypes.byref(params), px[0], px[1], ctypes.byref(rep),
                                           _stream(stream)))
-        return dict(epochs_done=rep.epochs_done, iterations_done=rep.iterations_done, objective=obj,
-                    epoch_ms=ms[:params.epochs])
+        return _report_dict(rep, keep, params)
 
+    def spdhg_autotune(self, reps=3, stream=None):
+        """Measures and sets the launch-shape knobs; returns {knob: value} (0 = built-in)."""
+        out = (ctypes.c_int * _capi.TUNE_KNOBS)()
+        self._check(_capi.lib().spdhg_autotune(self.h, int(reps), out, _stream(stream)))
+        return {k: out[i] for k, i in _capi.TUNE.items()}
 
     def spdhg_tune(self, knob, value):
-        """Sets a launch-shape knob ('prior_cols', 'prior_ychunk', 'fwd_split', 'bwd_cols'); 0 = default."""
+        """Sets a launch-shape knob ('prior_cols', 'prior_ychunk', 'fwd_split', 'fwd_warps'); 0 = default."""
         code = _capi.TUNE[knob] if isinstance(knob, str) else int(knob)
         self._check(_capi.lib().spdhg_tune(self.h, code, int(value)))
 
@@ -166,6 +167,46 @@ class Context:
         cnt = (ctypes.c_int64 * n)()
         self._check(_capi.lib().spdhg_profile_read(self.h, ms, cnt, n))
         return {k: (ms[i], cnt[i]) for i, k in enumerate(_capi.KERNELS)}
+
+
+def _report(params):
+    obj = np.full(params.epochs + 1, np.nan)
+    ms = np.zeros(max(params.epochs, 1))
+    rep = _capi.Report(0, 0, obj.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                       ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return rep, (obj, ms)
+
+
+def _report_dict(rep, keep, params):
+    obj, ms = keep
+    return dict(epochs_done=rep.epochs_done, iterations_done=rep.iterations_done, objective=obj,
+                epoch_ms=ms[:params.epochs])
+
+
+def spdhg_run_batch(contexts, params, xs=None, stream=None):
+    """One CUDA graph launch per epoch for all contexts (spdhg_run_batch); returns their reports."""
+    n = len(contexts)
+    if len(params) != n or (xs is not None and len(xs) != n):
+        raise ValueError("one params (and x) per context")
+    hs = (ctypes.c_void_p * n)(*[c.h for c in contexts])
+    ps = (_capi.Params * n)(*params)
+    reps = (_capi.Report * n)()
+    keeps = []
+    for r in range(n):
+        rep, keep = _report(params[r])
+        reps[r] = rep
+        keeps.append(keep)
+    xp = None
+    where = _capi.WHERE_DEVICE
+    if xs is not None:
+        pts = [_capi.pointer(x, c.n_voxels) for x, c in zip(xs, contexts)]
+        where = _same_where(*pts)
+        xp = (ctypes.c_void_p * n)(*[p for p, _ in pts])
+    code = _capi.lib().spdhg_run_batch(hs, ps, xp, where, n, reps, _stream(stream))
+    if code != _capi.OK:
+        msgs = "; ".join(_capi.lib().spdhg_last_error(c.h).decode() for c in contexts)
+        raise SpdhgError(code, msgs)
+    return [_report_dict(reps[r], keeps[r], params[r]) for r in range(n)]
 
 
 def spdhg_sample(seed, offset, n, probs):

@@ -24,9 +24,11 @@ _EXPORTS = [
     "spdhg_create", "spdhg_destroy", "spdhg_last_error", "spdhg_sizes", "spdhg_set_data",
     "spdhg_project", "spdhg_backproject", "spdhg_setup", "spdhg_iterate", "spdhg_get",
     "spdhg_objective", "spdhg_probabilities", "spdhg_sample", "spdhg_run", "spdhg_profile",
-    "spdhg_profile_read", "spdhg_backproject_noalloc", "spdhg_tune",
+    "spdhg_profile_read", "spdhg_backproject_noalloc", "spdhg_tune", "spdhg_autotune",
+    "spdhg_run_batch",
 ]
-TUNE = {"prior_cols": 0, "prior_ychunk": 1, "fwd_split": 2, "bwd_cols": 3}
+TUNE = {"prior_cols": 0, "prior_ychunk": 1, "fwd_split": 2, "fwd_warps": 3}
+TUNE_KNOBS = 8
 KERNELS = ["forward", "backward", "prior", "tgv", "w_step"]
 
 
@@ -54,7 +56,7 @@ class Params(ctypes.Structure):
         ("alpha1", ctypes.c_double), ("dtv_gamma", ctypes.c_double), ("dtv_eta_frac", ctypes.c_double),
         ("sampling", ctypes.c_int), ("precond", ctypes.c_int), ("rho", ctypes.c_double),
         ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64), ("epochs", ctypes.c_int),
-        ("objective_every", ctypes.c_int),
+        ("objective_every", ctypes.c_int), ("graph", ctypes.c_int),
     ]
 
 
@@ -101,6 +103,8 @@ def lib():
             "spdhg_profile_read": ([vp, P(dp), P(i64), i32], i32),
             "spdhg_backproject_noalloc": ([vp, vp, vp, i32, vp], i32),
             "spdhg_tune": ([vp, i32, i32], i32),
+            "spdhg_autotune": ([vp, i32, P(i32), vp], i32),
+            "spdhg_run_batch": ([P(vp), P(Params), P(vp), i32, i32, P(Report), vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -132,9 +136,9 @@ def make_geometry(sc):
 
 def make_params(prior="tv", alpha=0.1, alpha0=0.2, alpha1=0.1, dtv_gamma=0.995, dtv_eta_frac=0.01,
                 sampling="balanced", precond=True, rho=0.99, gamma=1.0, seed=1808, epochs=1,
-                objective_every=0):
+                objective_every=0, graph=False):
     return Params(PRIOR[prior], alpha, alpha0, alpha1, dtv_gamma, dtv_eta_frac, SAMPLING[sampling],
-                  int(bool(precond)), rho, gamma, seed, epochs, objective_every)
+                  int(bool(precond)), rho, gamma, seed, epochs, objective_every, int(bool(graph)))
 
 
 def pointer(a, numel=None, dtype=np.float32):

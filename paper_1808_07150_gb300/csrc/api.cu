@@ -159,6 +159,7 @@ int prepare_forward(spdhg_ctx* ctx, int subset, FwdArgs& a, cudaStream_t s) {
   const size_t lines = (size_t)subset_views(ctx->dg, subset) * ctx->dg.R;
   const size_t need = lines * split * ctx->dg.P;
   if (need > ctx->fwd_part_cap) {
+    ++ctx->graph_gen;  // captured iterations hold the old address
     if (ctx->fwd_part) cudaFree(ctx->fwd_part);
     ctx->fwd_part = nullptr;
     ctx->fwd_part_cap = 0;
@@ -166,6 +167,7 @@ int prepare_forward(spdhg_ctx* ctx, int subset, FwdArgs& a, cudaStream_t s) {
     ctx->fwd_part_cap = need;
   }
   if (lines > ctx->fwd_ticket_cap) {
+    ++ctx->graph_gen;
     if (ctx->fwd_tickets) cudaFree(ctx->fwd_tickets);
     ctx->fwd_tickets = nullptr;
     ctx->fwd_ticket_cap = 0;
@@ -182,6 +184,112 @@ int prepare_forward(spdhg_ctx* ctx, int subset, FwdArgs& a, cudaStream_t s) {
 }
 
 }  // namespace
+
+// Enqueues the kernels of one SPDHG iteration (Algorithm 2) on block i and advances the
+// ping-pong parities.  Used by spdhg_iterate and, under stream capture, by the epoch graphs.
+int spdhg::enqueue_block(spdhg_ctx* ctx, int i, cudaStream_t s) {
+  const int m = ctx->geom.n_subsets;
+  const spdhg_params& p = ctx->params;
+  const float inv_p = (float)(1.0 / ctx->probs[i]);
+  if (i < m) {
+    FwdArgs fa{};
+    fa.x = ctx->x[ctx->xcur];
+    fa.mult = ctx->has_mult ? ctx->mult : nullptr;
+    fa.b = ctx->b;
+    fa.r = ctx->r;
+    fa.y = ctx->y;
+    fa.wdy = ctx->wdy;
+    fa.sigma = ctx->sigma;
+    fa.gamma_rho = (float)(p.gamma * p.rho);
+    if (int st = prepare_forward(ctx, i, fa, s)) return st;
+    {
+      ProfScope ps(ctx, SPDHG_KERNEL_FORWARD, s);
+      CK(launch_forward(ctx->dg, i, FWD_DATA, fa, s));
+    }
+    BwdArgs ba{};
+    ba.w = ctx->wdy;
+    ba.x = ctx->x[ctx->xcur];
+    ba.z = ctx->z;
+    ba.T = ctx->T;
+    ba.inv_p = inv_p;
+    {
+      ProfScope ps(ctx, SPDHG_KERNEL_BACKWARD, s);
+      CK(launch_backward(ctx->dg, i, BWD_UPDATE, ba, s));
+    }
+    if (p.prior == SPDHG_PRIOR_TGV) {
+      ProfScope ps(ctx, SPDHG_KERNEL_WSTEP, s);
+      CK(launch_w_step(ctx->dg, ctx->w[ctx->wcur], ctx->zw, ctx->Tw, s));
+    }
+  } else if (p.prior == SPDHG_PRIOR_TGV) {
+    const int kblk = i - m;
+    TgvArgs ta{};
+    ta.block = kblk;
+    ta.u_in = ctx->x[ctx->xcur];
+    ta.u_out = ctx->x[1 - ctx->xcur];
+    ta.w_in = ctx->w[ctx->wcur];
+    ta.w_out = ctx->w[1 - ctx->wcur];
+    if (kblk == 0) {
+      ta.q_in = ctx->q[ctx->qcur];
+      ta.q_out = ctx->q[1 - ctx->qcur];
+      ta.alpha = (float)p.alpha0;
+    } else {
+      ta.q_in = ctx->q2[ctx->q2cur];
+      ta.q_out = ctx->q2[1 - ctx->q2cur];
+      ta.alpha = (float)p.alpha1;
+    }
+    ta.zu = ctx->z;
+    ta.zw = ctx->zw;
+    ta.Tu = ctx->T;
+    ta.Tw = ctx->Tw;
+    ta.sigma = ctx->sigma_prior[kblk];
+    ta.inv_p = inv_p;
+    {
+      ProfScope ps(ctx, SPDHG_KERNEL_TGV, s);
+      CK(launch_tgv(ctx->dg, ta, s));
+    }
+    ctx->xcur ^= 1;
+    ctx->wcur ^= 1;
+    if (kblk == 0) ctx->qcur ^= 1;
+    else ctx->q2cur ^= 1;
+  } else {
+    PriorArgs pa{};
+    pa.kind = p.prior;
+    pa.x_in = ctx->x[ctx->xcur];
+    pa.x_out = ctx->x[1 - ctx->xcur];
+    pa.q_in = ctx->q[ctx->qcur];
+    pa.q_out = ctx->q[1 - ctx->qcur];
+    pa.z = ctx->z;
+    pa.T = ctx->T;
+    pa.side = ctx->side;
+    pa.sigma = ctx->sigma_prior[0];
+    pa.alpha = (float)p.alpha;
+    pa.inv_p = inv_p;
+    pa.gamma_d = (float)p.dtv_gamma;
+    pa.eta2 = (float)ctx->eta2;
+    {
+      ProfScope ps(ctx, SPDHG_KERNEL_PRIOR, s);
+      CK(launch_prior(ctx->dg, pa, s));
+    }
+    ctx->xcur ^= 1;
+    ctx->qcur ^= 1;
+  }
+  ++ctx->iterations;
+  return SPDHG_OK;
+}
+
+int spdhg::forward_scratch(spdhg_ctx* ctx, int subset, FwdArgs& a, cudaStream_t s) {
+  return prepare_forward(ctx, subset, a, s);
+}
+
+// Allocates the forward row-split scratch of every subset now, so that no allocation or memset
+// happens while an iteration is captured into a graph.
+int spdhg::prepare_all_forward(spdhg_ctx* ctx, cudaStream_t s) {
+  for (int i = -1; i < ctx->geom.n_subsets; ++i) {
+    FwdArgs a{};
+    if (int st = prepare_forward(ctx, i, a, s)) return st;
+  }
+  return SPDHG_OK;
+}
 
 extern "C" {
 
@@ -345,6 +453,7 @@ void spdhg_destroy(spdhg_ctx* ctx) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
+  spdhg::graph_cache_free(ctx);
   delete ctx;
 }
 
@@ -397,6 +506,7 @@ int spdhg_set_data(spdhg_ctx* ctx, const float* b, const float* r, const float* 
   }
   ctx->has_data = true;
   ctx->is_setup = false;
+  ++ctx->graph_gen;  // mult may have switched between a buffer and none
   return SPDHG_OK;
 }
 
@@ -555,6 +665,18 @@ int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int
     ctx->eta2 = eta * eta;
   }
 
+  // captured graph iterations stay valid while the scalars their kernels receive do not change
+  {
+    std::vector<double> sig = {(double)p.prior, p.alpha, p.alpha0, p.alpha1, p.dtv_gamma, p.gamma * p.rho,
+                               ctx->eta2, (double)ctx->Tw, (double)p.sampling};
+    sig.insert(sig.end(), ctx->probs.begin(), ctx->probs.end());
+    sig.insert(sig.end(), ctx->sigma_prior.begin(), ctx->sigma_prior.end());
+    if (sig != ctx->graph_sig) {
+      ctx->graph_sig = sig;
+      ++ctx->graph_gen;
+    }
+  }
+
   // initial state: x = max(x0, 0), y = z = q = 0
   ctx->xcur = 0;
   ctx->qcur = 0;
@@ -588,98 +710,11 @@ int spdhg_iterate(spdhg_ctx* ctx, const int32_t* blocks, int n, void* stream) {
   if (!ctx || (n > 0 && !blocks) || n < 0) return SPDHG_ERR_ARG;
   if (!ctx->is_setup) return fail(ctx, SPDHG_ERR_STATE, "spdhg_setup must be called before spdhg_iterate");
   if (int st = check_device(ctx)) return st;
-  cudaStream_t s = (cudaStream_t)stream;
-  const int m = ctx->geom.n_subsets;
   const int nblk = (int)ctx->probs.size();
-  const spdhg_params& p = ctx->params;
-  for (int k = 0; k < n; ++k) {
-    const int i = blocks[k];
-    if (i < 0 || i >= nblk) return fail(ctx, SPDHG_ERR_ARG, "block index out of range");
-    const float inv_p = (float)(1.0 / ctx->probs[i]);
-    if (i < m) {
-      FwdArgs fa{};
-      fa.x = ctx->x[ctx->xcur];
-      fa.mult = ctx->has_mult ? ctx->mult : nullptr;
-      fa.b = ctx->b;
-      fa.r = ctx->r;
-      fa.y = ctx->y;
-      fa.wdy = ctx->wdy;
-      fa.sigma = ctx->sigma;
-      fa.gamma_rho = (float)(p.gamma * p.rho);
-      if (int st = prepare_forward(ctx, i, fa, s)) return st;
-      {
-        ProfScope ps(ctx, SPDHG_KERNEL_FORWARD, s);
-        CK(launch_forward(ctx->dg, i, FWD_DATA, fa, s));
-      }
-      BwdArgs ba{};
-      ba.w = ctx->wdy;
-      ba.x = ctx->x[ctx->xcur];
-      ba.z = ctx->z;
-      ba.T = ctx->T;
-      ba.inv_p = inv_p;
-      {
-        ProfScope ps(ctx, SPDHG_KERNEL_BACKWARD, s);
-        CK(launch_backward(ctx->dg, i, BWD_UPDATE, ba, s));
-      }
-      if (p.prior == SPDHG_PRIOR_TGV) {
-        ProfScope ps(ctx, SPDHG_KERNEL_WSTEP, s);
-        CK(launch_w_step(ctx->dg, ctx->w[ctx->wcur], ctx->zw, ctx->Tw, s));
-      }
-    } else if (p.prior == SPDHG_PRIOR_TGV) {
-      const int kblk = i - m;
-      TgvArgs ta{};
-      ta.block = kblk;
-      ta.u_in = ctx->x[ctx->xcur];
-      ta.u_out = ctx->x[1 - ctx->xcur];
-      ta.w_in = ctx->w[ctx->wcur];
-      ta.w_out = ctx->w[1 - ctx->wcur];
-      if (kblk == 0) {
-        ta.q_in = ctx->q[ctx->qcur];
-        ta.q_out = ctx->q[1 - ctx->qcur];
-        ta.alpha = (float)p.alpha0;
-      } else {
-        ta.q_in = ctx->q2[ctx->q2cur];
-        ta.q_out = ctx->q2[1 - ctx->q2cur];
-        ta.alpha = (float)p.alpha1;
-      }
-      ta.zu = ctx->z;
-      ta.zw = ctx->zw;
-      ta.Tu = ctx->T;
-      ta.Tw = ctx->Tw;
-      ta.sigma = ctx->sigma_prior[kblk];
-      ta.inv_p = inv_p;
-      {
-        ProfScope ps(ctx, SPDHG_KERNEL_TGV, s);
-        CK(launch_tgv(ctx->dg, ta, s));
-      }
-      ctx->xcur ^= 1;
-      ctx->wcur ^= 1;
-      if (kblk == 0) ctx->qcur ^= 1;
-      else ctx->q2cur ^= 1;
-    } else {
-      PriorArgs pa{};
-      pa.kind = p.prior;
-      pa.x_in = ctx->x[ctx->xcur];
-      pa.x_out = ctx->x[1 - ctx->xcur];
-      pa.q_in = ctx->q[ctx->qcur];
-      pa.q_out = ctx->q[1 - ctx->qcur];
-      pa.z = ctx->z;
-      pa.T = ctx->T;
-      pa.side = ctx->side;
-      pa.sigma = ctx->sigma_prior[0];
-      pa.alpha = (float)p.alpha;
-      pa.inv_p = inv_p;
-      pa.gamma_d = (float)p.dtv_gamma;
-      pa.eta2 = (float)ctx->eta2;
-      {
-        ProfScope ps(ctx, SPDHG_KERNEL_PRIOR, s);
-        CK(launch_prior(ctx->dg, pa, s));
-      }
-      ctx->xcur ^= 1;
-      ctx->qcur ^= 1;
-    }
-    ++ctx->iterations;
-  }
+  for (int k = 0; k < n; ++k)
+    if (blocks[k] < 0 || blocks[k] >= nblk) return fail(ctx, SPDHG_ERR_ARG, "block index out of range");
+  for (int k = 0; k < n; ++k)
+    if (int st = spdhg::enqueue_block(ctx, blocks[k], (cudaStream_t)stream)) return st;
   return SPDHG_OK;
 }
 
@@ -759,6 +794,7 @@ int spdhg_objective(spdhg_ctx* ctx, const float* x, int where, double out[3], vo
 int spdhg_run(spdhg_ctx* ctx, const spdhg_params* params, float* x_inout, int where, spdhg_report* rep,
               void* stream) {
   if (!ctx || !params || params->epochs < 0) return SPDHG_ERR_ARG;
+  if (params->graph) return spdhg_run_batch(&ctx, params, &x_inout, where, 1, rep, stream);
   cudaStream_t s = (cudaStream_t)stream;
   if (int st = spdhg_setup(ctx, params, x_inout, where, stream)) return st;
   const int m = ctx->geom.n_subsets;
@@ -828,11 +864,15 @@ int spdhg_tune(spdhg_ctx* ctx, int knob, int value) {
     case SPDHG_TUNE_FWD_SPLIT:
       if (value > 16) return fail(ctx, SPDHG_ERR_ARG, "forward split out of range");
       break;
-    case SPDHG_TUNE_BWD_COLS:
-      if (value != 0 && (value & (value - 1))) return fail(ctx, SPDHG_ERR_ARG, "backward cols must be a power of two");
+    case SPDHG_TUNE_FWD_WARPS:
+      if (value != 0 && value != 4 && value != 8 && value != 16)
+        return fail(ctx, SPDHG_ERR_ARG, "forward warps must be 4, 8 or 16");
+      if (value != 0 && (ctx->dg.n_runs + value - 1) / value > 4)
+        return fail(ctx, SPDHG_ERR_ARG, "too few forward warps for the planes of a line");
       break;
     default: break;
   }
+  if (ctx->dg.tune[knob] != value) ++ctx->graph_gen;
   ctx->dg.tune[knob] = value;
   return SPDHG_OK;
 }

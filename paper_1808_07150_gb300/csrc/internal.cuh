@@ -139,6 +139,18 @@ cudaError_t launch_prior_term(const DevGeom& g, int kind, const float* x, const 
 cudaError_t launch_side_max_grad(const DevGeom& g, const float* side, double* partial, int nblocks,
                                  double* out, cudaStream_t s);
 
+// ---------------------------------------------------------------------------------------
+// iteration driver (api.cu) and epoch graphs (graph.cu)
+// ---------------------------------------------------------------------------------------
+// enqueues the kernels of one SPDHG iteration on block i and advances the ping-pong parities
+int enqueue_block(spdhg_ctx* ctx, int i, cudaStream_t s);
+// row-split scratch of the forward projector for `subset` into a (allocated on first need)
+int forward_scratch(spdhg_ctx* ctx, int subset, FwdArgs& a, cudaStream_t s);
+// allocates the forward row-split scratch for the full projection and every subset
+int prepare_all_forward(spdhg_ctx* ctx, cudaStream_t s);
+struct GraphCache;
+void graph_cache_free(spdhg_ctx* ctx);
+
 }  // namespace spdhg
 
 // The opaque context of the C ABI.
@@ -198,4 +210,9 @@ struct spdhg_ctx {
   std::vector<cudaEvent_t> prof_pool;
   double prof_ms[SPDHG_KERNEL_KINDS] = {0, 0, 0, 0, 0};
   int64_t prof_n[SPDHG_KERNEL_KINDS] = {0, 0, 0, 0, 0};
+  // captured iteration templates of the epoch graphs; graph_gen changes whenever an argument
+  // the kernels receive (parameters, buffers, launch shapes) may have changed
+  spdhg::GraphCache* gcache = nullptr;
+  uint64_t graph_gen = 0;
+  std::vector<double> graph_sig;
 };

@@ -676,7 +676,8 @@ static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cu
 template <int NT, int MODE>
 static cudaError_t fwd_ppt(const DevGeom& g, int subset, const FwdArgs& a, cudaStream_t s) {
   const int split = forward_split(g, subset);
-  const int nwarps = g.n_runs < 16 ? (g.n_runs < 4 ? 4 : g.n_runs) : 16;  // >= 128 threads
+  const int nwarps = g.tune[SPDHG_TUNE_FWD_WARPS] ? g.tune[SPDHG_TUNE_FWD_WARPS]
+                                                  : (g.n_runs < 16 ? (g.n_runs < 4 ? 4 : g.n_runs) : 16);
   const int ppt = (g.n_runs + nwarps - 1) / nwarps;                      // runs per warp
   const int threads = nwarps * 32;
   switch (ppt) {

@@ -168,25 +168,36 @@ def tiny_3d(n_subsets: int = 2, steep: bool = False) -> Scanner:
                    name="tiny3d-steep" if steep else "tiny3d")
 
 
-def batch_geometries(seed: int, count: int = 16):
-    """Uneven 3-D problems: 96^3 .. 200x200x100 voxels, 120-252 views (direct + 2 oblique segments)."""
+def batch_geometries(seed: int, count: int = 16, small: bool = False):
+    """Uneven 3-D problems: 96^3 .. 200x200x100 voxels, 120-252 views (direct + 2 oblique segments).
+
+    small=True draws the same kind of scanner at test size: 24..48 pixels across, 10..16 slices,
+    24..40 views.
+    """
     rng = np.random.default_rng(seed)
     out = []
     for k in range(count):
-        nxy = int(rng.integers(96, 201))
-        nz = int(rng.integers(96 if nxy < 100 else 64, 101))
-        views = int(rng.integers(120, 253))
+        if small:
+            nxy = int(rng.integers(24, 49))
+            nz = int(rng.integers(10, 17))
+            views = int(rng.integers(24, 41))
+        else:
+            nxy = int(rng.integers(96, 201))
+            nz = int(rng.integers(96 if nxy < 100 else 64, 101))
+            views = int(rng.integers(120, 253))
         v = 2.0
         half = nxy * v / 2
         nr = nxy
         radius = math.ceil(math.hypot(half, half)) + 10.0
         # one direct segment and a +-tilted pair, planes on slice centres
-        n_ob = max(nz - 8, 1)
+        off = 2 if small else 4  # oblique planes start `off` slices in from either end
+        n_ob = max(nz - 2 * off, 1)
         z0 = -(nz - 1) * v / 2
         out.append(Scanner(nx=nxy, ny=nxy, nz=nz, vx=v, vy=v, vz=v, n_radial=nr, d_radial=v,
                            n_views=views, radius=radius, seg_n=(nz, n_ob, n_ob),
-                           seg_zmid0=(z0, z0 + 4 * v, z0 + 4 * v), seg_dzmid=(v, v, v),
-                           seg_dz=(0.0, 6 * v, -6 * v), n_subsets=max(views // 12, 1),
+                           seg_zmid0=(z0, z0 + off * v, z0 + off * v), seg_dzmid=(v, v, v),
+                           seg_dz=(0.0, 6 * v, -6 * v),
+                           n_subsets=max(views // (4 if small else 12), 1),
                            name=f"batch{k}-{nxy}x{nxy}x{nz}-{views}v"))
     return out
 
