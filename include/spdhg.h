@@ -201,8 +201,8 @@ enum { SPDHG_TUNE_PRIOR_COLS = 0,   /* prior kernel: voxel columns per block, in
 int spdhg_tune(spdhg_ctx* ctx, int knob, int value);
 
 /* Picks the launch-shape knobs of the context by measurement: for each knob in turn, every
- * admissible value is timed (CUDA events on `stream`, `reps` launches after one warm-up) on the
- * kernel it shapes, with the current state and data but scratch outputs (the reconstruction
+ * admissible value is timed (CUDA events on `stream`: best of three trials of `reps` launches,
+ * 10 if reps <= 0, after one warm-up) on the kernel it shapes, with the current state and data but scratch outputs (the reconstruction
  * state is not changed), and the fastest value is kept.  Requires spdhg_setup.  chosen (NULL or
  * SPDHG_TUNE_KNOBS ints) receives the resulting knob values (0 = built-in choice kept). */
 int spdhg_autotune(spdhg_ctx* ctx, int reps, int* chosen, void* stream);

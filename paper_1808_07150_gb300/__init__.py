@@ -146,7 +146,7 @@ class Context:
                                           _stream(stream)))
         return _report_dict(rep, keep, params)
 
-    def spdhg_autotune(self, reps=3, stream=None):
+    def spdhg_autotune(self, reps=10, stream=None):
         """Measures and sets the launch-shape knobs; returns {knob: value} (0 = built-in)."""
         out = (ctypes.c_int * _capi.TUNE_KNOBS)()
         self._check(_capi.lib().spdhg_autotune(self.h, int(reps), out, _stream(stream)))

@@ -5,7 +5,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "internal.cuh"
@@ -275,6 +278,26 @@ int spdhg::enqueue_block(spdhg_ctx* ctx, int i, cudaStream_t s) {
   }
   ++ctx->iterations;
   return SPDHG_OK;
+}
+
+cudaError_t spdhg::allow_dynamic_smem_fn(const void* kern, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> limit;  // (device, function) -> bytes allowed
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = limit.find({dev, kern});
+  if (it == limit.end()) {
+    int optin = 0;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    cudaFuncAttributes fa{};
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim)) != cudaSuccess) return e;
+    it = limit.emplace(std::make_pair(dev, kern), lim).first;
+  }
+  return smem <= (size_t)it->second ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 int spdhg::forward_scratch(spdhg_ctx* ctx, int subset, FwdArgs& a, cudaStream_t s) {

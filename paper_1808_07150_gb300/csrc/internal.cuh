@@ -46,6 +46,18 @@ struct DevGeom {
   int tune[SPDHG_TUNE_KNOBS];  // launch-shape overrides (0: built-in heuristic)
 };
 
+// Lets `kern` take more than 48 KB of dynamic shared memory.  The attribute belongs to the
+// function, not to a launch, so it is raised once per device to the largest value the function
+// admits (the opt-in maximum less its static shared memory) instead of to this launch's size:
+// launches and captured graph nodes of contexts with different sizes then never invalidate one
+// another.  Occupancy still follows each launch's own size.
+cudaError_t allow_dynamic_smem_fn(const void* kern, size_t smem);
+template <class K>
+cudaError_t allow_dynamic_smem(K kern, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return allow_dynamic_smem_fn(reinterpret_cast<const void*>(kern), smem);
+}
+
 // Views of subset i: i, i+m, ...  (subset < 0: all views).
 __host__ __device__ inline int subset_views(const DevGeom& g, int subset) {
   return subset < 0 ? g.V : (g.V - subset + g.m - 1) / g.m;

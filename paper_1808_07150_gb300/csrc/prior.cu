@@ -186,10 +186,8 @@ cudaError_t launch_prior(const DevGeom& g, const PriorArgs& a, cudaStream_t s) {
   dim3 grid((g.nx + cols - 2) / (cols - 1), (g.ny + ychunk - 1) / ychunk);
   const int threads = cols * zw * 32;
   auto launch = [&](auto kern) -> cudaError_t {
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = allow_dynamic_smem(kern, smem);
+    if (e != cudaSuccess) return e;
     kern<<<grid, threads, smem, s>>>(g, a, cols, ychunk);
     return cudaGetLastError();
   };

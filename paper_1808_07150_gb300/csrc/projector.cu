@@ -659,8 +659,8 @@ static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cu
                       (size_t)2 * g.n_seg * kFwdChunk * (sizeof(float4) + sizeof(int4)) + (size_t)ecap * sizeof(Entry);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   if (MODE == FWD_DATA && !a.sigma) return cudaErrorInvalidValue;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_forward<NT, PPT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = allow_dynamic_smem(k_forward<NT, PPT, MODE>, smem);
     if (e != cudaSuccess) return e;
   }
   const int lines = subset_views(g, subset) * g.R;
@@ -728,8 +728,8 @@ static cudaError_t bwd_launch(const DevGeom& g, int subset, const BwdArgs& a, cu
                       (size_t)kBwdWarps * g.nr_max * sizeof(PixItem) + (size_t)g.P * sizeof(int);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   auto kern = k_backward<NT, ZK, MODE>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = allow_dynamic_smem(kern, smem);
     if (e != cudaSuccess) return e;
   }
   dim3 grid((g.nx + kBwdTile - 1) / kBwdTile, (g.ny + kBwdTile - 1) / kBwdTile);

@@ -108,6 +108,12 @@ def test_batch_equals_solo_runs_and_oracle():
             np.testing.assert_array_equal(xb[k], xs, err_msg=scs[k].name)
             np.testing.assert_array_equal(reps[k]["objective"], rs["objective"], err_msg=scs[k].name)
             assert reps[k]["epochs_done"] == epochs[k]
+        # again, on the captured iterations cached by the first batch, after the solo runs of
+        # differently sized contexts have launched the same kernels with other shapes
+        xb2 = [x.copy() for x in x0s]
+        pkg.spdhg_run_batch(ctxs, params, xb2)
+        for k in range(len(ctxs)):
+            np.testing.assert_array_equal(xb2[k], xb[k], err_msg=scs[k].name)
     finally:
         for c in ctxs:
             c.close()
