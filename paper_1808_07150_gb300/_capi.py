@@ -26,6 +26,8 @@ _EXPORTS = [
     "spdhg_objective", "spdhg_probabilities", "spdhg_sample", "spdhg_run", "spdhg_profile",
     "spdhg_profile_read", "spdhg_backproject_noalloc", "spdhg_tune", "spdhg_autotune",
     "spdhg_run_batch",
+    "unet_gemm", "unet_device_error", "unet_create", "unet_destroy", "unet_last_error", "unet_num_params",
+    "unet_set_params", "unet_get_params", "unet_get_grads", "unet_forward", "unet_backward", "unet_adam_step",
 ]
 TUNE = {"prior_cols": 0, "prior_ychunk": 1, "fwd_split": 2, "fwd_warps": 3}
 TUNE_KNOBS = 8
@@ -105,6 +107,18 @@ def lib():
             "spdhg_tune": ([vp, i32, i32], i32),
             "spdhg_autotune": ([vp, i32, P(i32), vp], i32),
             "spdhg_run_batch": ([P(vp), P(Params), P(vp), i32, i32, P(Report), vp], i32),
+            "unet_gemm": ([vp, vp, vp, i32, i32, i32, i32, vp], i32),
+            "unet_device_error": ([vp], i32),
+            "unet_create": ([i32, P(i32), i32, i32, i32, P(vp)], i32),
+            "unet_destroy": ([vp], None),
+            "unet_last_error": ([vp], ctypes.c_char_p),
+            "unet_num_params": ([vp], i64),
+            "unet_set_params": ([vp, P(ctypes.c_float), i64], i32),
+            "unet_get_params": ([vp, P(ctypes.c_float), i64], i32),
+            "unet_get_grads": ([vp, P(ctypes.c_float), i64], i32),
+            "unet_forward": ([vp, vp, ctypes.c_float, vp, vp, vp], i32),
+            "unet_backward": ([vp, vp, vp, i32, P(dp), vp], i32),
+            "unet_adam_step": ([vp, ctypes.c_float, vp], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)

@@ -22,14 +22,20 @@ def capi():
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "spdhg.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(spdhg_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b((?:spdhg|unet)_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_every_declared_function_is_exported(capi):
     names = _declared()
-    assert len(names) >= 14
+    assert len(names) >= 30
+    assert "unet_forward" in names and "spdhg_run_batch" in names
     lib = ctypes.CDLL(capi.library_path())
     for n in names:
         assert hasattr(lib, n), n
@@ -82,3 +88,20 @@ def test_library_loading_fails_loudly_when_missing(tmp_path, monkeypatch):
     monkeypatch.setattr(_capi, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         _capi.lib()
+
+
+def test_unet_rejects_bad_shapes_before_touching_the_device(capi):
+    lib = capi.lib()
+    h = ctypes.c_void_p()
+    ch = (ctypes.c_int * 4)(16, 32, 64, 128)
+    assert lib.unet_create(1, ch, 16, 16, 16, ctypes.byref(h)) == capi.ERR_ARG       # one level
+    assert lib.unet_create(4, ch, 20, 16, 16, ctypes.byref(h)) == capi.ERR_ARG       # 20 % 8 != 0
+    bad = (ctypes.c_int * 2)(16, 24)                                                 # 24 % 16 != 0
+    assert lib.unet_create(2, bad, 16, 16, 16, ctypes.byref(h)) == capi.ERR_ARG
+    assert h.value is None
+    assert lib.unet_num_params(None) == -1
+    # GEMM sizes the tensor-core tile cannot take
+    p = ctypes.c_void_p(16)
+    assert lib.unet_gemm(p, p, p, 128, 24, 64, 0, None) == capi.ERR_ARG             # N % 16 != 0
+    assert lib.unet_gemm(p, p, p, 128, 16, 12, 0, None) == capi.ERR_ARG             # K % 8 != 0
+    assert lib.unet_gemm(p, p, p, 128, 512, 64, 0, None) == capi.ERR_ARG            # N > 256
