@@ -155,6 +155,14 @@ enum { SPDHG_STATE_X = 0, SPDHG_STATE_Z = 1, SPDHG_STATE_T = 2, SPDHG_STATE_Y = 
  * TGV W (3N), ZW (3N), Q2 (6N: xx,yy,zz,xy,xz,yz). */
 int spdhg_get(spdhg_ctx* ctx, int what, void* dst, int where, void* stream);
 
+/* Overwrites a state array from src (host or device per `where`), the counterpart of spdhg_get
+ * for resuming a run or changing its iterate: X (N floats, stored as max(src, 0): the primal
+ * iterate that opens the next iteration), Z, Y, Q and for TGV W, ZW, Q2.  T and SIGMA follow
+ * from the data and are rejected (SPDHG_ERR_ARG).  A consistent SPDHG state keeps z = A^T y
+ * (Algorithm 2); replacing X alone is always consistent, since any primal point may start the
+ * iteration.  Requires spdhg_setup. */
+int spdhg_set(spdhg_ctx* ctx, int what, const void* src, int where, void* stream);
+
 /* Psi(x) in FP64 (Problem "PET Reconstruction with Subsets"): out[0] = sum_j varphi_j((P x)_j)
  * (Eq. EQU:LOCALDISTANCE), out[1] = alpha R(x) for the prior of the last spdhg_setup (0 if none),
  * out[2] = out[0] + out[1].  x = NULL uses the context's current iterate (and w for TGV). */

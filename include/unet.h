@@ -52,9 +52,9 @@ int unet_get_params(unet_net* net, float* params, int64_t n);
 /* Accumulated gradients of the last unet_backward calls (sum over the accumulated samples). */
 int unet_get_grads(unet_net* net, float* grads, int64_t n);
 
-/* Forward pass on the FP32 image x (device, nx*ny*nz): input x/scale (scale > 0, e.g. the mean
- * of x).  pred (device, FP32, may be NULL) receives the prediction in units of scale, x0 (may be
- * NULL) scale * pred: the warm start. */
+/* Forward pass on the FP32 image x (device, nx*ny*nz): input x/s with s = scale if scale > 0,
+ * else s = mean(x) computed on the device.  pred (device, FP32, may be NULL) receives the
+ * prediction in units of s, x0 (may be NULL) s * pred: the warm start. */
 int unet_forward(unet_net* net, const float* x, float scale, float* pred, float* x0, void* stream);
 /* Backward pass of the last forward: loss = mean((pred - target/scale)^2) with target a device
  * FP32 image (or, when target is NULL, the gradient gpred of any loss with respect to pred).

@@ -126,6 +126,15 @@ class Context:
         self._check(_capi.lib().spdhg_get(self.h, code, pd[0], pd[1], _stream(stream)))
         return dst
 
+    def spdhg_set(self, what, src, stream=None):
+        code = STATE[what] if isinstance(what, str) else int(what)
+        N, M = self.n_voxels, self.n_bins
+        numel = {0: N, 1: N, 3: M, 4: 3 * N, 6: 3 * N, 7: 3 * N, 8: 6 * N}.get(code)
+        if numel is None:
+            raise ValueError(f"state array {what!r} cannot be set")
+        ps = _capi.pointer(src, numel)
+        self._check(_capi.lib().spdhg_set(self.h, code, ps[0], ps[1], _stream(stream)))
+
     def spdhg_objective(self, x=None, stream=None):
         px = _capi.pointer(x, self.n_voxels)
         out = (ctypes.c_double * 3)()

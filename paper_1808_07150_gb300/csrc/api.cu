@@ -770,6 +770,44 @@ int spdhg_get(spdhg_ctx* ctx, int what, void* dst, int where, void* stream) {
   }
 }
 
+int spdhg_set(spdhg_ctx* ctx, int what, const void* src, int where, void* stream) {
+  if (!ctx || !src || (where != SPDHG_WHERE_HOST && where != SPDHG_WHERE_DEVICE)) return SPDHG_ERR_ARG;
+  if (int st = check_device(ctx)) return st;
+  if (!ctx->is_setup) return fail(ctx, SPDHG_ERR_STATE, "no state before spdhg_setup");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = ctx->N, M = ctx->M;
+  const bool tgv = ctx->params.prior == SPDHG_PRIOR_TGV;
+  const float* f = static_cast<const float*>(src);
+  switch (what) {
+    case SPDHG_STATE_X: {
+      // the primal iterate that opens the next iteration: kept non-negative
+      float* dst = ctx->x[ctx->xcur];
+      if (where == SPDHG_WHERE_HOST) {
+        if (int st = copy_in(ctx, ctx->x[1 - ctx->xcur], f, N, where, s)) return st;
+        f = ctx->x[1 - ctx->xcur];
+      }
+      k_clamp_copy<<<grid_for(N), 256, 0, s>>>(dst, f, N);
+      CK(cudaGetLastError());
+      return SPDHG_OK;
+    }
+    case SPDHG_STATE_Z: return copy_in(ctx, ctx->z, f, N, where, s);
+    case SPDHG_STATE_Y: return copy_in(ctx, ctx->y, f, M, where, s);
+    case SPDHG_STATE_Q:
+      if (ctx->params.prior == SPDHG_PRIOR_NONE) return fail(ctx, SPDHG_ERR_STATE, "no prior dual");
+      return copy_in(ctx, ctx->q[ctx->qcur], f, 3 * N, where, s);
+    case SPDHG_STATE_W:
+      if (!tgv) return fail(ctx, SPDHG_ERR_STATE, "no TGV state");
+      return copy_in(ctx, ctx->w[ctx->wcur], f, 3 * N, where, s);
+    case SPDHG_STATE_ZW:
+      if (!tgv) return fail(ctx, SPDHG_ERR_STATE, "no TGV state");
+      return copy_in(ctx, ctx->zw, f, 3 * N, where, s);
+    case SPDHG_STATE_Q2:
+      if (!tgv) return fail(ctx, SPDHG_ERR_STATE, "no TGV state");
+      return copy_in(ctx, ctx->q2[ctx->q2cur], f, 6 * N, where, s);
+    default: return fail(ctx, SPDHG_ERR_ARG, "state array cannot be set (T and SIGMA follow from the data)");
+  }
+}
+
 int spdhg_objective(spdhg_ctx* ctx, const float* x, int where, double out[3], void* stream) {
   if (!ctx || !out) return SPDHG_ERR_ARG;
   if (int st = check_device(ctx)) return st;

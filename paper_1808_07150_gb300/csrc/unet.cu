@@ -36,8 +36,9 @@ constexpr int kMaxLevels = 5;
 // small kernels
 // ------------------------------------------------------------------------------------------
 
-__global__ void k_prep_input(const float* __restrict__ x, float inv_s, bf16* __restrict__ in0, float* __restrict__ xn,
-                             int64_t V) {
+__global__ void k_prep_input(const float* __restrict__ x, const float* __restrict__ inv_s_p, bf16* __restrict__ in0,
+                             float* __restrict__ xn, int64_t V) {
+  const float inv_s = *inv_s_p;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
     const float a = x[v] * inv_s;
     const bf16 h = __float2bfloat16_rn(a);
@@ -104,9 +105,10 @@ __global__ void k_head_fwd(const bf16* __restrict__ h, int C, const float* __res
 }
 
 // gpred = 2 (pred - t / s) / V and per-block partial sums of the squared error (FP64)
-__global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ t, float inv_s, float* __restrict__ gpred,
-                      int64_t V, double* __restrict__ part) {
+__global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ t, const float* __restrict__ inv_s_p,
+                      float* __restrict__ gpred, int64_t V, double* __restrict__ part) {
   __shared__ double red[256];
+  const float inv_s = *inv_s_p;
   double acc = 0.0;
   const float k = 2.f / (float)V;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
@@ -232,9 +234,33 @@ __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float
   }
 }
 
-__global__ void k_scale(const float* __restrict__ a, float s, float* __restrict__ out, int64_t n) {
+// out = a / inv_s (the warm start in image units)
+__global__ void k_unscale(const float* __restrict__ a, const float* __restrict__ inv_s_p, float* __restrict__ out,
+                          int64_t n) {
+  const float s = 1.f / *inv_s_p;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = a[i] * s;
+}
+
+// one block: inv_s = 1 / scale, or 1 / mean(x) when scale <= 0 (fixed-order FP64 sum)
+__global__ void k_inv_scale(const float* __restrict__ x, int64_t V, float scale, float* __restrict__ inv_s) {
+  __shared__ double red[256];
+  if (scale > 0.f) {
+    if (threadIdx.x == 0) *inv_s = 1.f / scale;
+    return;
+  }
+  double acc = 0.0;
+  for (int64_t v = threadIdx.x; v < V; v += blockDim.x) acc += x[v];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double m = red[0] / (double)V;
+    *inv_s = m > 1e-30 ? (float)(1.0 / m) : 1.f;
+  }
 }
 
 int blocks_for(int64_t n, int t = 256) {
@@ -287,7 +313,7 @@ struct unet_net {
   size_t part_cap = 0;
   double* lpart = nullptr;
   float* cpart = nullptr;                // column-sum partials
-  float inv_s = 1.f;
+  float* inv_s = nullptr;                // device: 1 / scale of the last forward
   std::string err;
 };
 
@@ -484,7 +510,7 @@ void unet_destroy(unet_net* net) {
     if (p.wb) cudaFree(p.wb);
   }
   void* ptrs[] = {net->w, net->g, net->m, net->v, net->in0, net->xn, net->pred, net->gpred, net->bottom, net->gA,
-                  net->gB, net->part, net->lpart, net->cpart};
+                  net->gB, net->part, net->lpart, net->cpart, net->inv_s};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (int l = 0; l < kMaxLevels; ++l) {
@@ -580,6 +606,7 @@ int unet_create(int levels, const int* channels, int ny, int nx, int nz, unet_ne
   A(zalloc(&net->gB, gmax));
   A(zalloc(&net->lpart, 1024));
   A(zalloc(&net->cpart, 128 * 256));
+  A(zalloc(&net->inv_s, 1));
   if (st != UNET_OK) {
     unet_destroy(net);
     return st;
@@ -662,11 +689,11 @@ int unet_get_grads(unet_net* net, float* host, int64_t n) {
 }
 
 int unet_forward(unet_net* net, const float* x, float scale, float* pred, float* x0, void* stream) {
-  if (!net || !x || !(scale > 0)) return UNET_ERR_ARG;
+  if (!net || !x || !(scale == scale)) return UNET_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int L = net->L;
   const int64_t V0 = net->V[0];
-  net->inv_s = 1.f / scale;
+  k_inv_scale<<<1, 256, 0, s>>>(x, V0, scale, net->inv_s);
   k_prep_input<<<blocks_for(V0), 256, 0, s>>>(x, net->inv_s, net->in0, net->xn, V0);
   UCK(cudaGetLastError());
   View h{net->in0, 8, 0, 8};
@@ -703,7 +730,7 @@ int unet_forward(unet_net* net, const float* x, float scale, float* pred, float*
   UCK(cudaGetLastError());
   if (pred) UCK(cudaMemcpyAsync(pred, net->pred, V0 * sizeof(float), cudaMemcpyDeviceToDevice, s));
   if (x0) {
-    k_scale<<<blocks_for(V0), 256, 0, s>>>(net->pred, scale, x0, V0);
+    k_unscale<<<blocks_for(V0), 256, 0, s>>>(net->pred, net->inv_s, x0, V0);
     UCK(cudaGetLastError());
   }
   return UNET_OK;

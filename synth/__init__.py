@@ -119,6 +119,14 @@ def config_3d(n_subsets: int = 21) -> Scanner:
                    seg_dz=(0.0,), n_subsets=n_subsets, name="cyl3d-128x128x64-180v128r64p")
 
 
+def config_3d_small(n_subsets: int = 8) -> Scanner:
+    """The 3-D configuration's scanner at test size: 32x32x16 voxels at 2 mm, 48 views x 32 radial
+    x 16 direct planes, R = 60 mm."""
+    return Scanner(nx=32, ny=32, nz=16, vx=2.0, vy=2.0, vz=2.0, n_radial=32, d_radial=2.0,
+                   n_views=48, radius=60.0, seg_n=(16,), seg_zmid0=(-15.0,), seg_dzmid=(2.0,),
+                   seg_dz=(0.0,), n_subsets=n_subsets, name="cyl3d-small-32x32x16-48v32r16p")
+
+
 MMR_SPAN11_SEGMENTS = (  # (first ring-sum, planes, nominal ring difference)
     (0, 127, 0), (6, 115, 11), (6, 115, -11), (17, 93, 22), (17, 93, -22),
     (28, 71, 33), (28, 71, -33), (39, 49, 44), (39, 49, -44), (50, 27, 55), (50, 27, -55),
