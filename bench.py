@@ -47,9 +47,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="set up the workload, run one data and one prior iteration, exit (ncu captures)")
-    ap.add_argument("--workload", default="mmr", choices=["mmr", "batch16"],
+    ap.add_argument("--workload", default="mmr", choices=["mmr", "batch16", "warmstart"],
                     help="mmr: the mMR-scale dTV reconstruction (default); batch16: 16 uneven "
-                         "reconstructions, one CUDA graph launch per epoch")
+                         "reconstructions, one CUDA graph launch per epoch; warmstart: the learned "
+                         "warm start (U-Net trained on SPDHG+ solutions, 128x128x64 scanner)")
+    ap.add_argument("--n-train", type=int, default=512)
+    ap.add_argument("--n-test", type=int, default=64)
+    ap.add_argument("--train-epochs", type=int, default=8)
     return ap.parse_args()
 
 
@@ -506,6 +510,180 @@ def run_batch(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------------
+# learned warm start: U-Net on the 3-D scanner, time to a 1e-3 gap against SPDHG+ from zero
+# ------------------------------------------------------------------------------------------
+
+WS_WORKLOAD = "warmstart-cyl3d-128x128x64-180v128r64p-tv-21subsets-unet16-32-64-128"
+
+
+def unet_flops_per_sample(shape, channels):
+    """Multiply-adds x 2 of one training step (forward, data and weight gradients) of every
+    convolution, with the true input channel count (1) of the first layer."""
+    ny, nx, nz = shape
+    L = len(channels)
+    V = [ny * nx * nz // 8 ** l for l in range(L)]
+    f = 0
+    cin = 1
+    for l in range(L):
+        a = V[l] * 27 * cin * channels[l]
+        b = V[l] * 27 * channels[l] * channels[l]
+        f += a * (2 if l == 0 else 3) + 3 * b       # no data gradient into the input
+        cin = channels[l]
+    for l in range(L - 2, -1, -1):
+        f += 3 * V[l + 1] * 8 * channels[l + 1] * channels[l]
+        f += 3 * V[l] * 27 * 2 * channels[l] * channels[l] + 3 * V[l] * 27 * channels[l] * channels[l]
+    return 2 * f
+
+
+def run_warmstart(args):
+    import torch
+
+    import paper_1808_07150_gb300 as pkg
+    import synth
+    from paper_1808_07150_gb300 import _build_ext, learned, warmstart as W
+    torch.cuda.set_device(0)
+    _build_ext.build()
+    sc = synth.config_3d()
+    k, ref_epochs, max_epochs, group = 2, 60, 30, 32
+    channels = (16, 32, 64, 128)
+    alpha = 0.05
+    seeds_train = list(range(args.n_train))
+    seeds_test = list(range(10000, 10000 + args.n_test))
+
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a, np.float32).ravel()).cuda()
+
+    def problem(seed):
+        return synth.make_problem(sc, seed, counts=3e7, bg_frac=0.1, with_mult=True, with_side=False,
+                                  n_ellipsoids=8)
+
+    def params(seed, **kw):
+        return pkg.make_params("tv", alpha=alpha, seed=SEED + seed, **kw)
+
+    t_data = time.perf_counter()
+    xk, xs, test_ctx, test_ref = [], [], [], []
+    for start in range(0, len(seeds_train) + len(seeds_test), group):
+        chunk = (seeds_train + seeds_test)[start:start + group]
+        ctxs = []
+        for s_ in chunk:
+            d = problem(s_)
+            c = pkg.Context(sc)
+            c.spdhg_set_data(to_dev(d["b"]), to_dev(d["r"]), to_dev(d["mult"]))
+            ctxs.append(c)
+        a, b = W.pairs(ctxs, [params(s_) for s_ in chunk], k, ref_epochs)
+        for c, s_, xa, xb in zip(ctxs, chunk, a, b):
+            if s_ < 10000:
+                xk.append(xa)
+                xs.append(xb)
+                c.close()
+            else:
+                test_ctx.append((c, s_, xa))
+                test_ref.append(xb)
+    t_data = time.perf_counter() - t_data
+
+    # training on the tensor cores
+    net = learned.UNet(sc.image_shape, channels)
+    net.init(SEED)
+    for _ in range(2):  # warm-up of every kernel
+        net.forward(xk[0], 0.0)
+        net.backward(xs[0], want_loss=False)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    losses = W.train(net, xk, xs, epochs=args.train_epochs, lr=1e-3, batch=4, seed=SEED)
+    ev1.record()
+    torch.cuda.synchronize()
+    train_ms = ev0.elapsed_time(ev1)
+    steps = args.train_epochs * len(xk)
+    flops = unet_flops_per_sample(sc.image_shape, channels)
+    achieved_tflops = flops * steps / (train_ms / 1e3) / 1e12
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    bf16_peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops") or 1700.0
+
+    # evaluation: epochs and solver time to a relative objective gap of 1e-3
+    res = {"plain": [], "continue": [], "restart": []}
+    net_ms = []
+    zero = torch.zeros(sc.n_voxels, device="cuda")
+    for (ctx, s_, xa), xref in zip(test_ctx, test_ref):
+        p = params(s_)
+        ctx.spdhg_setup(p, None)
+        psi0 = ctx.spdhg_objective(zero)[2]
+        psi_star = ctx.spdhg_objective(xref)[2]
+        obj, ms = W.run_epochs(ctx, p, max_epochs, 0)
+        psi_star = min(psi_star, float(obj.min()))
+        # checkpoints (cumulative solver ms, objective): after every epoch, and for the warm
+        # starts also right after the network (the objective at x0)
+        runs = {"plain": list(zip(np.cumsum(ms), obj[1:]))}
+        for mode in ("continue", "restart"):
+            ctx.spdhg_setup(p, None)
+            ok_, msk = W.run_epochs(ctx, p, k, 0)
+            x0 = torch.zeros(sc.n_voxels, device="cuda")
+            xcur = torch.zeros(sc.n_voxels, device="cuda")
+            ctx.spdhg_get("x", xcur)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            net.forward(xcur, 0.0, None, x0)
+            b.record()
+            torch.cuda.synchronize()
+            t_net = a.elapsed_time(b)
+            net_ms.append(t_net)
+            if mode == "continue":
+                W.continue_from(ctx, x0)
+            else:
+                W.restart_from(ctx, x0, "tv")
+            ow, msw = W.run_epochs(ctx, p, max_epochs - k, k)
+            psi_star = min(psi_star, float(ow.min()))
+            t0 = float(np.sum(msk)) + t_net
+            runs[mode] = (list(zip(np.cumsum(msk), ok_[1:])) + [(t0, ow[0])] +
+                          list(zip(t0 + np.cumsum(msw), ow[1:])))
+        for mode, chk in runs.items():
+            hit = [(i, t) for i, (t, o) in enumerate(chk) if (o - psi_star) / (psi0 - psi_star) <= GAP]
+            res[mode].append(hit[0] if hit else (None, None))
+    assert learned.device_error() == 0
+
+    def summary(v):
+        hit = [x for x in v if x[0] is not None]
+        return {"reached": len(hit), "of": len(v),
+                "mean_checkpoint": float(np.mean([x[0] + 1 for x in hit])) if hit else None,
+                "mean_ms": float(np.mean([x[1] for x in hit])) if hit else None}
+
+    summ = {m: summary(v) for m, v in res.items()}
+    best = min(("continue", "restart"), key=lambda m: summ[m]["mean_ms"] or 1e30)
+    line = {
+        "metric": METRIC, "value": summ[best]["mean_ms"], "unit": "ms to 1e-3 rel. objective gap (mean)",
+        "n_gpus": 1, "steps": steps, "warmup": 2, "ms_per_step": train_ms / steps,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (U-Net) / f32 (SPDHG+)",
+        "data": "synthetic",
+        "config": {"workload": WS_WORKLOAD, "train_problems": len(xk), "test_problems": len(test_ctx),
+                   "k_epochs_before_net": k, "reference_epochs": ref_epochs, "train_epochs": args.train_epochs,
+                   "step": "value: mean solver time to gap 1e-3 with the learned warm start; ms_per_step: one "
+                           "U-Net training step (forward + backward) on one 128x128x64 sample"},
+        "time_to_gap": {"plain_zero_start": summ["plain"], "warm_continue": summ["continue"],
+                        "warm_restart": summ["restart"], "best_warm": best,
+                        "speedup_mean_ms": (summ["plain"]["mean_ms"] / summ[best]["mean_ms"])
+                        if summ["plain"]["mean_ms"] and summ[best]["mean_ms"] else None,
+                        "net_inference_ms": float(np.mean(net_ms))},
+        "training": {"loss_first_epoch": losses[0], "loss_last_epoch": losses[-1], "ms_total": train_ms,
+                     "samples_per_s": steps / (train_ms / 1e3), "data_generation_s": t_data},
+        "roofline": {"bound": "tensor", "kernel": "k_igemm (all U-Net convolution passes, one training step)",
+                     "achieved": achieved_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / bf16_peak, "traffic": None,
+                     "algorithmic_flops_per_step": flops,
+                     "note": "whole training step (incl. pooling, head, loss, Adam) timed; of measured bf16 peak"},
+    }
+    print(json.dumps(line), flush=True)
+    net.close()
+    for c, _, _ in test_ctx:
+        c.close()
+    return 0
+
+
 def run_ncu_case():
     """Few launches on the full workload: setup (252 sensitivity backprojections), then one data
     iteration (k_forward, k_backward) and one dTV prior iteration (k_prior)."""
@@ -538,6 +716,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch16":
         return run_batch(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
     return run_ours(args)
 
 

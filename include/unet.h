@@ -49,6 +49,9 @@ int64_t unet_num_params(const unet_net* net);
 /* Host vectors of unet_num_params floats.  set_params also resets the Adam moments. */
 int unet_set_params(unet_net* net, const float* params, int64_t n);
 int unet_get_params(unet_net* net, float* params, int64_t n);
+/* He-normal initialisation from `seed`: weights ~ N(0, 2 / fan_in), biases and head zero (the
+ * untrained network returns its input: x0 = x).  Resets the Adam moments. */
+int unet_init(unet_net* net, uint64_t seed);
 /* Accumulated gradients of the last unet_backward calls (sum over the accumulated samples). */
 int unet_get_grads(unet_net* net, float* grads, int64_t n);
 

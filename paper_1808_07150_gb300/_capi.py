@@ -27,7 +27,7 @@ _EXPORTS = [
     "spdhg_profile_read", "spdhg_backproject_noalloc", "spdhg_tune", "spdhg_autotune",
     "spdhg_run_batch", "spdhg_set",
     "unet_gemm", "unet_device_error", "unet_create", "unet_destroy", "unet_last_error", "unet_num_params",
-    "unet_set_params", "unet_get_params", "unet_get_grads", "unet_forward", "unet_backward", "unet_adam_step",
+    "unet_set_params", "unet_init", "unet_get_params", "unet_get_grads", "unet_forward", "unet_backward", "unet_adam_step",
 ]
 TUNE = {"prior_cols": 0, "prior_ychunk": 1, "fwd_split": 2, "fwd_warps": 3}
 TUNE_KNOBS = 8
@@ -116,6 +116,7 @@ def lib():
             "unet_num_params": ([vp], i64),
             "unet_set_params": ([vp, P(ctypes.c_float), i64], i32),
             "unet_get_params": ([vp, P(ctypes.c_float), i64], i32),
+            "unet_init": ([vp, u64], i32),
             "unet_get_grads": ([vp, P(ctypes.c_float), i64], i32),
             "unet_forward": ([vp, vp, ctypes.c_float, vp, vp, vp], i32),
             "unet_backward": ([vp, vp, vp, i32, P(dp), vp], i32),

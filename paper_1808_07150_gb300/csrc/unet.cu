@@ -655,6 +655,35 @@ int unet_set_params(unet_net* net, const float* host, int64_t n) {
   return UNET_OK;
 }
 
+// He-normal initialisation: weights ~ N(0, 2 / fan_in) (fan_in = cin * 27 for conv3, cin * 8 for
+// the transposed convolution), biases and head zero, so the untrained network is the identity
+// warm start pred = x/s.  Normal draws: Box-Muller on SplitMix64 uniforms (53-bit).
+int unet_init(unet_net* net, uint64_t seed) {
+  if (!net) return UNET_ERR_ARG;
+  uint64_t k = 0;
+  auto uniform = [&]() {
+    uint64_t z = seed + (++k) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return ((z >> 11) + 0.5) * (1.0 / 9007199254740992.0);  // (0, 1)
+  };
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<float> v((size_t)unet_num_params(net));
+  size_t q = 0;
+  for (const Param& p : net->P) {
+    const size_t nw = p.kind == 0 ? (size_t)p.cout * p.cin_true * 27 : p.kind == 1 ? (size_t)8 * p.cout * p.cin : p.cin_true;
+    const double sd = p.kind == 2 ? 0.0 : sqrt(2.0 / (p.kind == 0 ? 27.0 * p.cin_true : 8.0 * p.cin));
+    for (size_t i = 0; i < nw; ++i) {
+      const double r = sqrt(-2.0 * log(uniform())), t = two_pi * uniform();
+      v[q++] = (float)(sd * r * cos(t));
+    }
+    const int nb = p.kind == 2 ? 1 : p.cout;
+    for (int i = 0; i < nb; ++i) v[q++] = 0.f;
+  }
+  return unet_set_params(net, v.data(), (int64_t)v.size());
+}
+
 static int copy_vector_out(unet_net* net, const float* dsrc, float* host, int64_t n) {
   if (!net || !host || n != unet_num_params(net)) return UNET_ERR_ARG;
   std::vector<float> dev(net->n_master);

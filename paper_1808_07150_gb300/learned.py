@@ -58,6 +58,10 @@ class UNet:
             raise ValueError(f"expected {self.n_params} parameters, got {vec.size}")
         self._check(_capi.lib().unet_set_params(self.h, vec.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), vec.size))
 
+    def init(self, seed):
+        """He-normal weights, zero biases and head (the untrained network is the identity)."""
+        self._check(_capi.lib().unet_init(self.h, int(seed)))
+
     def get_params(self):
         out = np.empty(self.n_params, np.float32)
         self._check(_capi.lib().unet_get_params(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), out.size))

@@ -29,7 +29,7 @@ from concurrent.futures import ThreadPoolExecutor
 import numpy as np
 
 __all__ = [
-    "Scanner", "config_2d", "config_3d", "config_mmr", "tiny_2d", "tiny_3d", "batch_geometries",
+    "Scanner", "config_2d", "config_3d", "config_3d_small", "config_mmr", "tiny_2d", "tiny_3d", "batch_geometries",
     "Ellipsoid", "random_phantom", "voxelize", "analytic_projection", "smooth_multipliers",
     "side_image", "make_problem", "random_image", "random_sinogram", "subset_views",
 ]
@@ -297,9 +297,13 @@ def _view_lors(g: Scanner, v: int):
     return o, d, h
 
 
-def _project_view(g: Scanner, ells, v: int):
-    o, d, h = _view_lors(g, v)
-    hh = h[:, None]
+def _project_views(g: Scanner, ells, v0: int, v1: int):
+    """Exact chords of views v0..v1-1 (the same elementwise arithmetic for every bin as one view
+    at a time, so the result does not depend on the grouping)."""
+    parts = [_view_lors(g, v) for v in range(v0, v1)]
+    o = np.stack([q[0] for q in parts], axis=1)              # (3, G, R, P)
+    d = np.stack([q[1] for q in parts], axis=1)
+    hh = parts[0][2][None, :, None]                          # h depends on the radial bin only
     dnorm = np.sqrt((d * d).sum(0))
     acc = np.zeros(o.shape[1:])
     for e in ells:
@@ -325,12 +329,15 @@ def analytic_projection(g: Scanner, ells, threads: int = 0):
     """Exact line integrals of the continuous phantom along every LOR (voxel-size units)."""
     out = np.empty(g.sino_shape, np.float64)
     workers = threads or min(32, max(1, (__import__("os").cpu_count() or 1)))
+    group = max(1, min(g.n_views, (1 << 18) // max(1, g.n_radial * g.n_planes)))
+    starts = list(range(0, g.n_views, group))
 
-    def work(v):
-        out[v] = _project_view(g, ells, v)
+    def work(v0):
+        v1 = min(g.n_views, v0 + group)
+        out[v0:v1] = _project_views(g, ells, v0, v1)
 
     with ThreadPoolExecutor(workers) as ex:
-        list(ex.map(work, range(g.n_views)))
+        list(ex.map(work, starts))
     return out
 
 
