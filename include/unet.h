@@ -30,7 +30,7 @@ int unet_gemm(const uint16_t* a, const uint16_t* b, float* d, int M, int N, int 
 typedef struct unet_net unet_net;
 
 /* A 3-D U-Net for volumes of ny x nx x nz voxels (each divisible by 2^(levels-1)), 2 <= levels
- * <= 5, channels[l] in {16, 32, ..., 128}.  Encoder level l: conv3 + ReLU, conv3 + ReLU (3x3x3,
+ * <= 5, channels[l] in {16, 32, 64, 128}.  Encoder level l: conv3 + ReLU, conv3 + ReLU (3x3x3,
  * zero padding; 2x2x2 max-pooling before every level but the first); decoder level l = levels-2
  * .. 0: 2x2x2 stride-2 transposed convolution of the level below, concatenated [up, skip] with
  * the encoder output of level l, conv3 + ReLU, conv3 + ReLU; head pred = x/s + sum_c w_c h_c + b.

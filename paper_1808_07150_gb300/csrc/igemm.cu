@@ -3,11 +3,15 @@
 // data and weight gradients) and a plain GEMM used to check the operand layouts.
 //
 // One CTA computes a 128 x N tile of D = A B^T (N = output channels, 16..256, a multiple of 16).
-// The reduction runs in chunks of 64 elements through a two-stage shared-memory ring: all 128
-// threads stage the chunk's A (128 x 64) and B (N x 64) tiles with 16-byte cp.async copies
-// (zero-filled outside the volume, so padding costs no branch in the MMA), one thread issues four
-// tcgen05.mma (K = 16 each) and commits them to the stage's mbarrier, and the ring slot is reused
-// once that mbarrier reports the MMAs that read it complete.  The epilogue reads the accumulator
+// The reduction runs in chunks of 64 elements through a shared-memory ring (2 slots, the next
+// chunk's copies in flight while the current one is multiplied; deeper rings measured slower
+// because they halve the CTAs per SM that hide the gather latency): all 128 threads stage a
+// chunk's A (128 x 64) and B (N x 64) tiles with 16-byte cp.async copies (zero-filled outside the
+// volume, so padding costs no branch in the MMA), one thread issues four tcgen05.mma (K = 16
+// each) and commits them to the slot's mbarrier, and a slot is refilled once that mbarrier
+// reports the MMAs that read it complete.  Thread t always stages row t of the A tile, so the
+// voxel of the row, its in-volume taps (a bit mask) and the tap offsets (a shared table) are
+// computed once per CTA: the gather itself is shifts and adds.  The epilogue reads the accumulator
 // from TMEM (tcgen05.ld, one row per thread) and applies bias, ReLU and a ReLU-gradient mask.
 //
 // Operands are gathered from channels-last BF16 tensors (element (v, c) at p[v * stride + off + c]):
@@ -27,7 +31,8 @@ namespace ig {
 
 constexpr int BM = 128;     // rows per CTA tile
 constexpr int BK = 64;      // reduction elements per stage
-constexpr int STAGES = 2;
+constexpr int STAGES = 2;   // shared-memory ring slots
+constexpr int DIST = 1;     // tiles in flight ahead of the one being multiplied
 constexpr int THREADS = 128;
 constexpr long long WAIT_CYCLES = 4000000000ll;  // ~2 s at 2 GHz: a lost completion ends the kernel
 
@@ -45,86 +50,16 @@ __device__ __forceinline__ Vox decomp(int v, int nx, int nz) {
   return r;
 }
 
-// ---- operand chunk addressing: returns the source pointer and whether the chunk exists ----
-
-// A, K-major: chunk (row r, k-block kb) = A[r][8 kb .. 8 kb + 7]
-template <int AM>
-__device__ __forceinline__ const __nv_bfloat16* a_chunk_k(const GemmArgs& g, int r, int kb, bool& ok) {
-  ok = false;
-  if (r >= g.M || kb * 8 >= g.K) return g.a;
-  if (AM == A_GEMM_K) {
-    ok = true;
-    return g.a + (size_t)r * g.a_stride + kb * 8;
-  } else if (AM == A_ROWS) {
-    ok = true;
-    return g.a + (size_t)r * g.a_stride + g.a_off + kb * 8;
-  } else if (AM == A_CONV3) {
-    const int c8 = g.a_c >> 3;
-    const int tap = kb / c8, cg = kb - tap * c8;
-    const Vox p = decomp(r, g.nx, g.nz);
-    const int yy = p.y + tap / 9 - 1, xx = p.x + (tap / 3) % 3 - 1, zz = p.z + tap % 3 - 1;
-    if (yy < 0 || yy >= g.ny || xx < 0 || xx >= g.nx || zz < 0 || zz >= g.nz) return g.a;
-    ok = true;
-    return g.a + ((size_t)(yy * g.nx + xx) * g.nz + zz) * g.a_stride + g.a_off + cg * 8;
-  } else {  // A_CHILD8: child o of coarse voxel r on the grid (2 ny, 2 nx, 2 nz)
-    const int c8 = g.a_c >> 3;
-    const int o = kb / c8, cg = kb - o * c8;
-    const Vox p = decomp(r, g.nx, g.nz);
-    const int fy = 2 * p.y + (o >> 2), fx = 2 * p.x + ((o >> 1) & 1), fz = 2 * p.z + (o & 1);
-    ok = true;
-    return g.a + ((size_t)(fy * 2 * g.nx + fx) * (2 * g.nz) + fz) * g.a_stride + g.a_off + cg * 8;
-  }
-}
-
-// A, MN-major: chunk (reduction index k, row block mb) = A[8 mb .. 8 mb + 7][k]
-template <int AM>
-__device__ __forceinline__ const __nv_bfloat16* a_chunk_mn(const GemmArgs& g, int k, int mb, int kend, bool& ok) {
-  ok = false;
-  const int m0 = mb * 8;
-  if (m0 >= g.M || k >= kend) return g.a;
-  if (AM == A_GEMM_MN) {
-    ok = true;
-    return g.a + (size_t)k * g.a_stride + m0;
-  } else if (AM == A_WG_CONV3) {  // rows (tap, c), reduction over voxels v = k
-    const int tap = m0 / g.a_c, c0 = m0 - tap * g.a_c;
-    const Vox p = decomp(k, g.nx, g.nz);
-    const int yy = p.y + tap / 9 - 1, xx = p.x + (tap / 3) % 3 - 1, zz = p.z + tap % 3 - 1;
-    if (yy < 0 || yy >= g.ny || xx < 0 || xx >= g.nx || zz < 0 || zz >= g.nz) return g.a;
-    ok = true;
-    return g.a + ((size_t)(yy * g.nx + xx) * g.nz + zz) * g.a_stride + g.a_off + c0;
-  } else {  // A_WG_TCONV: rows c, reduction over coarse voxels p = k
-    ok = true;
-    return g.a + (size_t)k * g.a_stride + g.a_off + m0;
-  }
-}
-
-// B, K-major: chunk (column n, k-block kb) = B[n][8 kb ..]; per-z weight slices at b_zstride
-template <int BMODE>
-__device__ __forceinline__ const __nv_bfloat16* b_chunk_k(const GemmArgs& g, int n, int kb, bool& ok) {
-  ok = n < g.N && kb * 8 < g.K;
-  if (!ok) return g.b;
-  return g.b + (size_t)blockIdx.z * g.b_zstride + (size_t)n * g.b_stride + kb * 8;
-}
-
-// B, MN-major: chunk (reduction index k, column block nb) = B[8 nb .. 8 nb + 7][k]
-template <int BMODE>
-__device__ __forceinline__ const __nv_bfloat16* b_chunk_mn(const GemmArgs& g, int k, int nb, int kend, bool& ok) {
-  ok = false;
-  const int n0 = nb * 8;
-  if (n0 >= g.N || k >= kend) return g.b;
-  if (BMODE == B_GEMM_MN) {
-    ok = true;
-    return g.b + (size_t)k * g.b_stride + n0;
-  } else if (BMODE == B_WG_ROWS) {
-    ok = true;
-    return g.b + (size_t)k * g.b_stride + g.b_off + n0;
-  } else {  // B_WG_CHILD: gradient at child o = blockIdx.z of coarse voxel k
-    const int o = blockIdx.z;
-    const Vox p = decomp(k, g.nx, g.nz);
-    const int fy = 2 * p.y + (o >> 2), fx = 2 * p.x + ((o >> 1) & 1), fz = 2 * p.z + (o & 1);
-    ok = true;
-    return g.b + ((size_t)(fy * 2 * g.nx + fx) * (2 * g.nz) + fz) * g.b_stride + g.b_off + n0;
-  }
+// Bit t (t = 9 (dy+1) + 3 (dx+1) + (dz+1)) is set when the 3x3x3 neighbour at (dy, dx, dz) of
+// voxel (y, x, z) lies inside the (ny, nx, nz) grid.
+__device__ __forceinline__ uint32_t tap_mask(int y, int x, int z, const GemmArgs& g) {
+  const uint32_t my = (y > 0 ? 1u : 0u) | 2u | (y + 1 < g.ny ? 4u : 0u);
+  const uint32_t mx = (x > 0 ? 1u : 0u) | 2u | (x + 1 < g.nx ? 4u : 0u);
+  const uint32_t mz = (z > 0 ? 1u : 0u) | 2u | (z + 1 < g.nz ? 4u : 0u);
+  uint32_t m = 0;
+#pragma unroll
+  for (int t = 0; t < 27; ++t) m |= ((my >> (t / 9)) & (mx >> ((t / 3) % 3)) & (mz >> (t % 3)) & 1u) << t;
+  return m;
 }
 
 __device__ __forceinline__ void set_error(int code) { atomicCAS(&g_error, 0, code); }
@@ -137,7 +72,7 @@ __global__ void __launch_bounds__(THREADS) k_igemm(GemmArgs g) {
   __shared__ uint64_t mbar[STAGES];
   __shared__ uint32_t tmem_slot;
 
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int NP = (g.N + 15) & ~15;                     // columns of the MMA (multiple of 16)
   const uint32_t a_bytes = BM * BK * 2, b_bytes = (uint32_t)NP * BK * 2;
   const uint32_t sbase = umma::smem_u32(smem);
@@ -149,6 +84,10 @@ __global__ void __launch_bounds__(THREADS) k_igemm(GemmArgs g) {
   uint32_t ncols = 32;
   while ((int)ncols < NP) ncols <<= 1;
 
+  // linear offset of every 3x3x3 tap and of every 2x2x2 child (on the 2x grid), for the gathers
+  __shared__ int s_tap[27], s_child[8];
+  if (tid < 27) s_tap[tid] = ((tid / 9 - 1) * g.nx + (tid / 3) % 3 - 1) * g.nz + tid % 3 - 1;
+  if (tid < 8) s_child[tid] = ((tid >> 2) * 2 * g.nx + ((tid >> 1) & 1)) * (2 * g.nz) + (tid & 1);
   if (warp == 0) umma::tmem_alloc(&tmem_slot, ncols);
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) umma::mbar_init(&mbar[s], 1);
@@ -168,56 +107,124 @@ __global__ void __launch_bounds__(THREADS) k_igemm(GemmArgs g) {
   const uint32_t b_kstep = B_MN ? 2u * NP * 16 : 256u;
   const uint32_t idesc = umma::idesc_bf16(BM, NP, A_MN, B_MN);
 
-  bool failed = false;
-  for (int kt = 0; kt < ktiles; ++kt) {
-    const int s = kt % STAGES;
-    if (kt >= STAGES) {
-      const bool ok = umma::mbar_wait(&mbar[s], ((kt / STAGES) - 1) & 1, WAIT_CYCLES);
-      if (__syncthreads_or(!ok)) {  // the whole block leaves together
-        failed = true;
-        break;
+  // ---- gather state: the tile height equals the thread count, so thread t stages row t of every
+  // K-major A tile, and reduction index t % 64 of every MN-major tile ----
+  const int csh = __ffs(g.a_c >> 3) - 1;   // a_c / 8 = 2^csh (channel counts are powers of two)
+  const int ash = __ffs(g.a_c) - 1;        // a_c = 2^ash
+  const int r = row0 + tid;
+  const bool rok = r < g.M;
+  int a_row = r;                           // CHILD8: fine index of child 0 of row r
+  uint32_t amask = 0;                      // CONV3: taps of row r inside the volume
+  if (!A_MN && rok && (AM == A_CONV3 || AM == A_CHILD8)) {
+    const Vox p = decomp(r, g.nx, g.nz);
+    if (AM == A_CONV3) amask = tap_mask(p.y, p.x, p.z, g);
+    else a_row = ((2 * p.y) * 2 * g.nx + 2 * p.x) * (2 * g.nz) + 2 * p.z;
+  }
+
+  // issues the cp.async copies of reduction tile t into its ring slot
+  auto load_tile = [&](int t) {
+    const uint32_t sa = sbase + (t % STAGES) * (a_bytes + b_bytes), sb = sa + a_bytes;
+    const int k0 = kbeg + t * BK;
+    if (!A_MN) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {  // A: row r, k blocks j of the tile
+        const int kb = (k0 >> 3) + j;
+        bool ok = rok && kb * 8 < kend;
+        const __nv_bfloat16* src = g.a;
+        if (AM == A_GEMM_K) {
+          src = g.a + (size_t)r * g.a_stride + kb * 8;
+        } else if (AM == A_ROWS) {
+          src = g.a + (size_t)r * g.a_stride + g.a_off + kb * 8;
+        } else if (AM == A_CONV3) {
+          const int tap = kb >> csh, cg = kb & ((1 << csh) - 1);
+          ok = ok && tap < 27 && ((amask >> tap) & 1u);
+          if (ok) src = g.a + (size_t)(r + s_tap[tap]) * g.a_stride + g.a_off + cg * 8;
+        } else {  // A_CHILD8
+          const int o = kb >> csh, cg = kb & ((1 << csh) - 1);
+          ok = ok && o < 8;
+          if (ok) src = g.a + (size_t)(a_row + s_child[o]) * g.a_stride + g.a_off + cg * 8;
+        }
+        umma::cp16(sa + ((tid >> 3) * 8 + j) * 128 + (tid & 7) * 16, ok ? src : g.a, ok ? 16u : 0u);
+      }
+    } else {
+      const int kk = tid & (BK - 1), k = k0 + kk;
+      const bool kok = k < kend;
+      uint32_t kmask = 0;
+      if (AM == A_WG_CONV3 && kok) {
+        const Vox p = decomp(k, g.nx, g.nz);
+        kmask = tap_mask(p.y, p.x, p.z, g);
+      }
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {  // A: reduction index k, row blocks (tid / 64) + 2 it
+        const int rb = (tid >> 6) + 2 * it;
+        const int m0 = row0 + rb * 8;
+        bool ok = kok && m0 < g.M;
+        const __nv_bfloat16* src = g.a;
+        if (AM == A_GEMM_MN) {
+          src = g.a + (size_t)k * g.a_stride + m0;
+        } else if (AM == A_WG_CONV3) {  // rows (tap, c): 8 consecutive rows share one tap
+          const int tap = m0 >> ash, c0 = m0 & (g.a_c - 1);
+          ok = ok && ((kmask >> tap) & 1u);
+          if (ok) src = g.a + (size_t)(k + s_tap[tap]) * g.a_stride + g.a_off + c0;
+        } else {  // A_WG_TCONV
+          src = g.a + (size_t)k * g.a_stride + g.a_off + m0;
+        }
+        umma::cp16(sa + ((kk >> 3) * (BM / 8) + rb) * 128 + (kk & 7) * 16, ok ? src : g.a, ok ? 16u : 0u);
       }
     }
-    const uint32_t sa = sbase + s * (a_bytes + b_bytes), sb = sa + a_bytes;
-    const int k0 = kbeg + kt * BK;
-    // stage A: 1024 chunks
-    for (int idx = tid; idx < BM * 8; idx += THREADS) {
-      bool ok;
-      const __nv_bfloat16* src;
-      uint32_t dst;
-      if (!A_MN) {
-        const int i = idx & (BM - 1), j = idx >> 7;  // row, k block
-        src = a_chunk_k<AM>(g, row0 + i, (k0 >> 3) + j, ok);
-        if (k0 + j * 8 >= kend) ok = false;
-        dst = sa + ((i >> 3) * 8 + j) * 128 + (i & 7) * 16;
-      } else {
-        const int kk = idx & (BK - 1), rb = idx >> 6;  // reduction index, row block
-        src = a_chunk_mn<AM>(g, k0 + kk, (row0 >> 3) + rb, kend, ok);
-        dst = sa + ((kk >> 3) * (BM / 8) + rb) * 128 + (kk & 7) * 16;
-      }
-      umma::cp16(dst, src, ok ? 16u : 0u);
-    }
-    // stage B: NP * 8 chunks
-    for (int idx = tid; idx < NP * 8; idx += THREADS) {
-      bool ok;
-      const __nv_bfloat16* src;
-      uint32_t dst;
-      if (!B_MN) {
+    if (!B_MN) {
+      for (int idx = tid; idx < NP * 8; idx += THREADS) {  // B: NP * 8 chunks
         const int i = idx % NP, j = idx / NP;
-        src = b_chunk_k<BMODE>(g, i, (k0 >> 3) + j, ok);
-        if (k0 + j * 8 >= kend) ok = false;
-        dst = sb + ((i >> 3) * 8 + j) * 128 + (i & 7) * 16;
-      } else {
-        const int kk = idx & (BK - 1), nb = idx >> 6;
-        src = b_chunk_mn<BMODE>(g, k0 + kk, nb, kend, ok);
-        dst = sb + ((kk >> 3) * (NP / 8) + nb) * 128 + (kk & 7) * 16;
+        const int kb = (k0 >> 3) + j;
+        const bool ok = i < g.N && kb * 8 < kend;
+        const __nv_bfloat16* src = g.b + (size_t)blockIdx.z * g.b_zstride + (size_t)i * g.b_stride + kb * 8;
+        umma::cp16(sb + ((i >> 3) * 8 + j) * 128 + (i & 7) * 16, ok ? src : g.b, ok ? 16u : 0u);
       }
-      umma::cp16(dst, src, ok ? 16u : 0u);
+    } else {
+      const int kk = tid & (BK - 1), k = k0 + kk;
+      const bool kok = k < kend;
+      int brow = k;
+      if (BMODE == B_WG_CHILD && kok) {
+        const Vox p = decomp(k, g.nx, g.nz);
+        brow = ((2 * p.y) * 2 * g.nx + 2 * p.x) * (2 * g.nz) + 2 * p.z + s_child[blockIdx.z];
+      }
+      for (int it = 0; it < NP / 16; ++it) {  // B: reduction index k, column blocks (tid / 64) + 2 it
+        const int nb = (tid >> 6) + 2 * it;
+        const int n0 = nb * 8;
+        const bool ok = kok && n0 < g.N;
+        const __nv_bfloat16* src = BMODE == B_GEMM_MN ? g.b + (size_t)k * g.b_stride + n0
+                                                      : g.b + (size_t)brow * g.b_stride + g.b_off + n0;
+        umma::cp16(sb + ((kk >> 3) * (NP / 8) + nb) * 128 + (kk & 7) * 16, ok ? src : g.b, ok ? 16u : 0u);
+      }
     }
-    umma::cp_commit_wait_all();
+  };
+
+  bool failed = false;
+  // prologue: tiles 0 .. DIST-1 in flight (one copy group per tile, empty past the end)
+  for (int t = 0; t < DIST; ++t) {
+    if (t < ktiles) load_tile(t);
+    umma::cp_commit();
+  }
+  for (int kt = 0; kt < ktiles; ++kt) {
+    const int nt = kt + DIST;
+    if (nt < ktiles) {
+      if (nt >= STAGES) {
+        // the slot of tile nt last held tile nt - STAGES: its MMAs must have completed
+        const int prev = nt - STAGES;
+        const bool ok = umma::mbar_wait(&mbar[prev % STAGES], (prev / STAGES) & 1, WAIT_CYCLES);
+        if (__syncthreads_or(!ok)) {  // the whole block leaves together
+          failed = true;
+          break;
+        }
+      }
+      load_tile(nt);
+    }
+    umma::cp_commit();
+    umma::cp_wait<DIST>();  // tile kt has landed (this thread's copies)
     umma::fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
+      const uint32_t sa = sbase + (kt % STAGES) * (a_bytes + b_bytes), sb = sa + a_bytes;
       umma::fence_after_sync();
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
@@ -225,9 +232,10 @@ __global__ void __launch_bounds__(THREADS) k_igemm(GemmArgs g) {
         const uint64_t bd = umma::smem_desc(sb + kk * b_kstep, b_lbo, b_sbo);
         umma::mma_bf16(tmem, ad, bd, idesc, (kt > 0 || kk > 0) ? 1u : 0u);
       }
-      umma::commit(&mbar[s]);
+      umma::commit(&mbar[kt % STAGES]);
     }
   }
+  umma::cp_wait<0>();
   // every MMA of the tile completes before the last commit's mbarrier phase
   if (!failed && ktiles > 0) {
     const int last = ktiles - 1;
@@ -244,8 +252,8 @@ __global__ void __launch_bounds__(THREADS) k_igemm(GemmArgs g) {
   umma::fence_after_sync();
 
   // ---- epilogue: warp w holds rows 32 w .. 32 w + 31 (TMEM lanes), one row per thread ----
-  const int r = row0 + warp * 32 + lane;
-  const bool row_ok = r < g.M && !failed;
+  // (row r = row0 + 32 warp + lane = row0 + tid, as in the gathers)
+  const bool row_ok = rok && !failed;
   const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
   for (int n0 = 0; n0 < NP; n0 += 8) {
     float v[8];
@@ -313,6 +321,9 @@ cudaError_t launch(int am, int bm, int em, const GemmArgs& g, dim3 grid, cudaStr
   if (g.N < 16 || g.N > 256 || (g.N & 15) || g.M <= 0 || g.K <= 0) return cudaErrorInvalidValue;
   if ((a_k || b_k) && (g.K & 7)) return cudaErrorInvalidValue;
   if (!a_k && (g.M & 7)) return cudaErrorInvalidValue;
+  // the gathers decode (tap, channel) with shifts: channel counts are powers of two (>= 8)
+  const bool gather = am == A_CONV3 || am == A_CHILD8 || am == A_WG_CONV3 || am == A_WG_TCONV;
+  if (gather && (g.a_c < 8 || (g.a_c & (g.a_c - 1)))) return cudaErrorInvalidValue;
 #define IG_CASE(A, B, E) \
   if (am == A && bm == B && em == E) return launch_t<A, B, E>(g, grid, s);
   IG_CASE(A_GEMM_K, B_GEMM_K, E_F32)

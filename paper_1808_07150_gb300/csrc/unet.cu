@@ -31,6 +31,7 @@ typedef __nv_bfloat16 bf16;
 namespace {
 
 constexpr int kMaxLevels = 5;
+constexpr int kColsumBlocks = 1024;  // blocks of the column sums (bias gradients)
 
 // ------------------------------------------------------------------------------------------
 // small kernels
@@ -242,15 +243,29 @@ __global__ void k_unscale(const float* __restrict__ a, const float* __restrict__
     out[i] = a[i] * s;
 }
 
-// one block: inv_s = 1 / scale, or 1 / mean(x) when scale <= 0 (fixed-order FP64 sum)
-__global__ void k_inv_scale(const float* __restrict__ x, int64_t V, float scale, float* __restrict__ inv_s) {
+// inv_s = 1 / scale, or 1 / mean(x) when scale <= 0: per-block FP64 partial sums in a fixed
+// order, then one block adds the partials in a fixed order
+constexpr int kMeanBlocks = 256;
+__global__ void k_sum_part(const float* __restrict__ x, int64_t V, double* __restrict__ part) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) acc += x[v];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+__global__ void k_inv_scale(const double* __restrict__ part, int nparts, int64_t V, float scale, float* __restrict__ inv_s) {
   __shared__ double red[256];
   if (scale > 0.f) {
     if (threadIdx.x == 0) *inv_s = 1.f / scale;
     return;
   }
   double acc = 0.0;
-  for (int64_t v = threadIdx.x; v < V; v += blockDim.x) acc += x[v];
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i];
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -402,7 +417,7 @@ int split_count(int64_t K, int tiles) {
 int colsum(unet_net* net, View gv, int64_t V, float* out, int accumulate, cudaStream_t s) {
   const int C = gv.c;
   const int threads = C >= 256 ? 256 : (256 / C) * C;
-  const int nb = 128;
+  const int nb = kColsumBlocks;
   k_colsum_part<bf16><<<nb, threads, threads * sizeof(float), s>>>(gv.p, gv.stride, gv.off, C, V, nullptr, net->cpart);
   k_sum_parts<<<(C + 127) / 128, 128, 0, s>>>(net->cpart, nb, C, out, accumulate);
   UCK(cudaGetLastError());
@@ -526,7 +541,7 @@ int unet_create(int levels, const int* channels, int ny, int nx, int nz, unet_ne
   *out = nullptr;
   if (levels < 2 || levels > kMaxLevels || !channels) return UNET_ERR_ARG;
   for (int l = 0; l < levels; ++l)
-    if (channels[l] < 16 || channels[l] > 128 || (channels[l] & 15)) return UNET_ERR_ARG;
+    if (channels[l] < 16 || channels[l] > 128 || (channels[l] & (channels[l] - 1))) return UNET_ERR_ARG;
   const int f = 1 << (levels - 1);
   if (ny <= 0 || nx <= 0 || nz <= 0 || ny % f || nx % f || nz % f) return UNET_ERR_ARG;
   unet_net* net = new unet_net();
@@ -605,7 +620,7 @@ int unet_create(int levels, const int* channels, int ny, int nx, int nz, unet_ne
   A(zalloc(&net->gA, gmax));
   A(zalloc(&net->gB, gmax));
   A(zalloc(&net->lpart, 1024));
-  A(zalloc(&net->cpart, 128 * 256));
+  A(zalloc(&net->cpart, (size_t)kColsumBlocks * 256));
   A(zalloc(&net->inv_s, 1));
   if (st != UNET_OK) {
     unet_destroy(net);
@@ -722,7 +737,8 @@ int unet_forward(unet_net* net, const float* x, float scale, float* pred, float*
   cudaStream_t s = (cudaStream_t)stream;
   const int L = net->L;
   const int64_t V0 = net->V[0];
-  k_inv_scale<<<1, 256, 0, s>>>(x, V0, scale, net->inv_s);
+  if (!(scale > 0)) k_sum_part<<<kMeanBlocks, 256, 0, s>>>(x, V0, net->lpart);
+  k_inv_scale<<<1, 256, 0, s>>>(net->lpart, kMeanBlocks, V0, scale, net->inv_s);
   k_prep_input<<<blocks_for(V0), 256, 0, s>>>(x, net->inv_s, net->in0, net->xn, V0);
   UCK(cudaGetLastError());
   View h{net->in0, 8, 0, 8};
@@ -792,10 +808,11 @@ int unet_backward(unet_net* net, const float* target, const float* gpred_in, int
   const int c0 = net->ch[0];
   {
     const int threads = (256 / c0) * c0;
-    k_colsum_part<bf16><<<128, threads, threads * sizeof(float), s>>>(net->db[0], c0, 0, c0, V0, net->gpred, net->cpart);
-    k_sum_parts<<<1, 128, 0, s>>>(net->cpart, 128, c0, net->g + hd.off_w, accumulate);
-    k_colsum_part<float><<<128, 256, 256 * sizeof(float), s>>>(net->gpred, 1, 0, 1, V0, nullptr, net->cpart);
-    k_sum_parts<<<1, 32, 0, s>>>(net->cpart, 128, 1, net->g + hd.off_b, accumulate);
+    k_colsum_part<bf16><<<kColsumBlocks, threads, threads * sizeof(float), s>>>(net->db[0], c0, 0, c0, V0, net->gpred,
+                                                                                net->cpart);
+    k_sum_parts<<<1, 128, 0, s>>>(net->cpart, kColsumBlocks, c0, net->g + hd.off_w, accumulate);
+    k_colsum_part<float><<<kColsumBlocks, 256, 256 * sizeof(float), s>>>(net->gpred, 1, 0, 1, V0, nullptr, net->cpart);
+    k_sum_parts<<<1, 32, 0, s>>>(net->cpart, kColsumBlocks, 1, net->g + hd.off_b, accumulate);
     k_head_bwd<<<blocks_for(V0 * c0), 256, 0, s>>>(net->gpred, net->db[0], c0, net->w + hd.off_w, net->gA, V0);
     UCK(cudaGetLastError());
   }

@@ -96,7 +96,7 @@ def test_unet_rejects_bad_shapes_before_touching_the_device(capi):
     ch = (ctypes.c_int * 4)(16, 32, 64, 128)
     assert lib.unet_create(1, ch, 16, 16, 16, ctypes.byref(h)) == capi.ERR_ARG       # one level
     assert lib.unet_create(4, ch, 20, 16, 16, ctypes.byref(h)) == capi.ERR_ARG       # 20 % 8 != 0
-    bad = (ctypes.c_int * 2)(16, 24)                                                 # 24 % 16 != 0
+    bad = (ctypes.c_int * 2)(16, 48)                                                 # 48: not a power of two
     assert lib.unet_create(2, bad, 16, 16, 16, ctypes.byref(h)) == capi.ERR_ARG
     assert h.value is None
     assert lib.unet_num_params(None) == -1
