@@ -47,13 +47,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true",
                     help="set up the workload, run one data and one prior iteration, exit (ncu captures)")
+    ap.add_argument("--ncu-unet", action="store_true",
+                    help="three U-Net training steps on a 128x128x64 volume, exit (ncu captures)")
     ap.add_argument("--workload", default="mmr", choices=["mmr", "batch16", "warmstart"],
                     help="mmr: the mMR-scale dTV reconstruction (default); batch16: 16 uneven "
                          "reconstructions, one CUDA graph launch per epoch; warmstart: the learned "
                          "warm start (U-Net trained on SPDHG+ solutions, 128x128x64 scanner)")
     ap.add_argument("--n-train", type=int, default=512)
     ap.add_argument("--n-test", type=int, default=64)
-    ap.add_argument("--train-epochs", type=int, default=8)
+    ap.add_argument("--train-epochs", type=int, default=16)
+    ap.add_argument("--k", type=int, default=2, help="warm start: SPDHG+ epochs before the network")
     return ap.parse_args()
 
 
@@ -545,7 +548,7 @@ def run_warmstart(args):
     torch.cuda.set_device(0)
     _build_ext.build()
     sc = synth.config_3d()
-    k, ref_epochs, max_epochs, group = 2, 60, 30, 32
+    k, ref_epochs, max_epochs, group = args.k, 60, 30, 32
     channels = (16, 32, 64, 128)
     alpha = 0.05
     seeds_train = list(range(args.n_train))
@@ -609,6 +612,7 @@ def run_warmstart(args):
     # evaluation: epochs and solver time to a relative objective gap of 1e-3
     res = {"plain": [], "continue": [], "restart": []}
     net_ms = []
+    gap_xk, gap_x0, dist_ratio = [], [], []
     zero = torch.zeros(sc.n_voxels, device="cuda")
     for (ctx, s_, xa), xref in zip(test_ctx, test_ref):
         p = params(s_)
@@ -634,6 +638,10 @@ def run_warmstart(args):
             t_net = a.elapsed_time(b)
             net_ms.append(t_net)
             if mode == "continue":
+                gap_xk.append(float((ok_[-1] - psi_star) / (psi0 - psi_star)))
+                gap_x0.append(float((ctx.spdhg_objective(torch.clamp(x0, min=0))[2] - psi_star) / (psi0 - psi_star)))
+                dist_ratio.append(float(torch.linalg.vector_norm(torch.clamp(x0, min=0) - xref) /
+                                        torch.linalg.vector_norm(xcur - xref)))
                 W.continue_from(ctx, x0)
             else:
                 W.restart_from(ctx, x0, "tv")
@@ -668,7 +676,10 @@ def run_warmstart(args):
                         "warm_restart": summ["restart"], "best_warm": best,
                         "speedup_mean_ms": (summ["plain"]["mean_ms"] / summ[best]["mean_ms"])
                         if summ["plain"]["mean_ms"] and summ[best]["mean_ms"] else None,
-                        "net_inference_ms": float(np.mean(net_ms))},
+                        "net_inference_ms": float(np.mean(net_ms)),
+                        "median_gap_at_x_k": float(np.median(gap_xk)), "median_gap_at_x0": float(np.median(gap_x0)),
+                        "mean_dist_x0_over_dist_x_k_to_x_star": float(np.mean(dist_ratio)),
+                        "note": "gaps use the Psi* of each problem as finally estimated"},
         "training": {"loss_first_epoch": losses[0], "loss_last_epoch": losses[-1], "ms_total": train_ms,
                      "samples_per_s": steps / (train_ms / 1e3), "data_generation_s": t_data},
         "roofline": {"bound": "tensor", "kernel": "k_igemm (all U-Net convolution passes, one training step)",
@@ -708,10 +719,36 @@ def run_ncu_case():
     return 0
 
 
+def run_ncu_unet():
+    """Three training steps (forward, backward, Adam) of the 16-32-64-128 U-Net on a 128x128x64
+    volume of seeded random values: the launches ncu captures for the tensor-core kernels."""
+    import torch
+
+    from paper_1808_07150_gb300 import _build_ext, learned
+    torch.cuda.set_device(0)
+    _build_ext.build()
+    shape = (128, 128, 64)
+    r = np.random.default_rng(SEED)
+    x = torch.from_numpy(r.random(shape).astype(np.float32).ravel()).cuda()
+    t = torch.from_numpy(r.random(shape).astype(np.float32).ravel()).cuda()
+    with learned.UNet(shape, (16, 32, 64, 128)) as net:
+        net.init(SEED)
+        for _ in range(3):
+            net.forward(x, 0.0)
+            net.backward(t, want_loss=False)
+            net.adam_step(1e-3)
+        torch.cuda.synchronize()
+        assert learned.device_error() == 0
+    print("ncu unet case done")
+    return 0
+
+
 def main():
     args = parse()
     if args.ncu_case:
         return run_ncu_case()
+    if args.ncu_unet:
+        return run_ncu_unet()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch16":

@@ -165,12 +165,19 @@ __global__ void k_colsum_part(const T* __restrict__ src, int stride, int off, in
 }
 
 // out[c] (+)= sum_b part[b][c]
+// one block per column c, 256 threads: strided partial sums, then a fixed-order tree
 __global__ void k_sum_parts(const float* __restrict__ part, int nb, int C, float* __restrict__ out, int accumulate) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= C) return;
+  __shared__ float red[256];
+  const int c = blockIdx.x;
   float s = 0.f;
-  for (int b = 0; b < nb; ++b) s += part[(size_t)b * C + c];
-  out[c] = accumulate ? out[c] + s : s;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(size_t)b * C + c];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = accumulate ? out[c] + red[0] : red[0];
 }
 
 // conv3 weight gradient: part[split][tap * cin + ci][co] -> g[co][tap][ci] (+)=
@@ -419,7 +426,7 @@ int colsum(unet_net* net, View gv, int64_t V, float* out, int accumulate, cudaSt
   const int threads = C >= 256 ? 256 : (256 / C) * C;
   const int nb = kColsumBlocks;
   k_colsum_part<bf16><<<nb, threads, threads * sizeof(float), s>>>(gv.p, gv.stride, gv.off, C, V, nullptr, net->cpart);
-  k_sum_parts<<<(C + 127) / 128, 128, 0, s>>>(net->cpart, nb, C, out, accumulate);
+  k_sum_parts<<<C, 256, 0, s>>>(net->cpart, nb, C, out, accumulate);
   UCK(cudaGetLastError());
   return UNET_OK;
 }
@@ -810,9 +817,9 @@ int unet_backward(unet_net* net, const float* target, const float* gpred_in, int
     const int threads = (256 / c0) * c0;
     k_colsum_part<bf16><<<kColsumBlocks, threads, threads * sizeof(float), s>>>(net->db[0], c0, 0, c0, V0, net->gpred,
                                                                                 net->cpart);
-    k_sum_parts<<<1, 128, 0, s>>>(net->cpart, kColsumBlocks, c0, net->g + hd.off_w, accumulate);
+    k_sum_parts<<<c0, 256, 0, s>>>(net->cpart, kColsumBlocks, c0, net->g + hd.off_w, accumulate);
     k_colsum_part<float><<<kColsumBlocks, 256, 256 * sizeof(float), s>>>(net->gpred, 1, 0, 1, V0, nullptr, net->cpart);
-    k_sum_parts<<<1, 32, 0, s>>>(net->cpart, kColsumBlocks, 1, net->g + hd.off_b, accumulate);
+    k_sum_parts<<<1, 256, 0, s>>>(net->cpart, kColsumBlocks, 1, net->g + hd.off_b, accumulate);
     k_head_bwd<<<blocks_for(V0 * c0), 256, 0, s>>>(net->gpred, net->db[0], c0, net->w + hd.off_w, net->gA, V0);
     UCK(cudaGetLastError());
   }
