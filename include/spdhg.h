@@ -198,10 +198,12 @@ int spdhg_backproject_noalloc(spdhg_ctx* ctx, const float* y, float* x, int subs
 
 /* Launch-shape knobs of the iteration kernels (0 restores the built-in choice).  They change
  * only how work is split across threads and blocks, never the arithmetic. */
-enum { SPDHG_TUNE_PRIOR_COLS = 0,   /* prior kernel: voxel columns per block, incl. one halo column */
+enum { SPDHG_TUNE_PRIOR_COLS = 0,   /* prior kernel: voxel columns per block, incl. one halo column
+                                       (blocks of up to 32 warps) */
        SPDHG_TUNE_PRIOR_YCHUNK = 1, /* prior kernel: rows marched per block */
        SPDHG_TUNE_FWD_SPLIT = 2,    /* forward kernel: blocks sharing the planes of one LOR line */
        SPDHG_TUNE_FWD_WARPS = 3,    /* forward kernel: warps per block (4, 8 or 16) */
+       SPDHG_TUNE_PRIOR_STAGES = 4, /* prior kernel: rows in its shared-memory pipeline (3 or 4) */
        SPDHG_TUNE_KNOBS = 8 };
 
 /* Sets one launch-shape knob of the context (value 0: default).  Out-of-range values are rejected

@@ -917,7 +917,10 @@ int spdhg_tune(spdhg_ctx* ctx, int knob, int value) {
   const int zw = (ctx->dg.nz + 31) / 32;
   switch (knob) {
     case SPDHG_TUNE_PRIOR_COLS:
-      if (value != 0 && (value < 2 || value * zw > 16)) return fail(ctx, SPDHG_ERR_ARG, "prior cols out of range");
+      if (value != 0 && (value < 2 || value * zw > 32)) return fail(ctx, SPDHG_ERR_ARG, "prior cols out of range");
+      break;
+    case SPDHG_TUNE_PRIOR_STAGES:
+      if (value != 0 && value != 3 && value != 4) return fail(ctx, SPDHG_ERR_ARG, "prior stages must be 3 or 4");
       break;
     case SPDHG_TUNE_PRIOR_YCHUNK:
       if (value > 1 << 20) return fail(ctx, SPDHG_ERR_ARG, "ychunk out of range");

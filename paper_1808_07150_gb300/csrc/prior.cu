@@ -61,17 +61,17 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-constexpr int kPriorStages = 4;  // rows resident or in flight: iy, iy+1 (used), iy+2, iy+3 (loading)
+// Row pipeline depth STAGES: rows iy and iy + 1 are used, the next STAGES - 2 rows are loading.
 
 // One block owns `cols - 1` voxel columns in x (plus one halo column on the lower side whose
 // duals are recomputed, not written) and the whole z extent (warps along z, so every access is
 // a contiguous 128-byte line), and marches along y over `ychunk` rows (plus one warm-up row).
-// Rows are staged in shared memory by a 4-stage cp.async pipeline: each thread copies its own
+// Rows are staged in shared memory by a STAGES-deep cp.async pipeline: each thread copies its own
 // voxel's operands (x, v also for one upper halo column), neighbours are read from the staged
 // rows, the lower y neighbour's dual change is carried in a register and the lower x / z
 // neighbours' through shared memory.  Every array is read from HBM once per row.
-template <int KIND>
-__global__ void __launch_bounds__(512) k_prior(DevGeom g, PriorArgs a, int cols, int ychunk) {
+template <int KIND, int STAGES>
+__global__ void __launch_bounds__(1024) k_prior(DevGeom g, PriorArgs a, int cols, int ychunk) {
   extern __shared__ float sh[];
   const int zw = (g.nz + 31) >> 5;
   const int zc = zw * 32;                     // staged z extent
@@ -94,12 +94,12 @@ __global__ void __launch_bounds__(512) k_prior(DevGeom g, PriorArgs a, int cols,
   // stage layout: x, v: (cols + 1) x zc; q0, q1, q2, z, T: cols x zc
   const int xv_sz = (cols + 1) * zc, cell_sz = cols * zc;
   const int stage_sz = 2 * xv_sz + 5 * cell_sz;
-  float* sbx = sh + kPriorStages * stage_sz;  // [cols][zc] b_x of the current row
+  float* sbx = sh + STAGES * stage_sz;        // [cols][zc] b_x of the current row
   float* sbz = sbx + cell_sz;                 // [cols][zc] b_z of the current row
   const int me = c * zc + iz;
 
   auto issue_row = [&](int row) {
-    float* st = sh + (row % kPriorStages) * stage_sz;
+    float* st = sh + (row % STAGES) * stage_sz;
     const int base = row * sy + ix * nz + iz;  // only dereferenced when valid
     cp_async4(st + me, a.x_in, base, live);
     if (dtv) cp_async4(st + xv_sz + me, a.side, base, live);
@@ -117,18 +117,18 @@ __global__ void __launch_bounds__(512) k_prior(DevGeom g, PriorArgs a, int cols,
     }
   };
 
-  for (int k = 0; k < kPriorStages - 1; ++k) {
+  for (int k = 0; k < STAGES - 1; ++k) {
     if (ys + k <= ylast) issue_row(ys + k);
     cp_async_commit();
   }
   float by_prev = 0.f;
   for (int iy = ys; iy < y1; ++iy) {
-    if (iy + kPriorStages - 1 <= ylast) issue_row(iy + kPriorStages - 1);
+    if (iy + STAGES - 1 <= ylast) issue_row(iy + STAGES - 1);
     cp_async_commit();
-    cp_async_wait<kPriorStages - 2>();  // rows iy and iy + 1 have landed
+    cp_async_wait<STAGES - 2>();  // rows iy and iy + 1 have landed
     __syncthreads();
-    const float* st = sh + (iy % kPriorStages) * stage_sz;
-    const float* sn = sh + ((iy + 1) % kPriorStages) * stage_sz;
+    const float* st = sh + (iy % STAGES) * stage_sz;
+    const float* sn = sh + ((iy + 1) % STAGES) * stage_sz;
     const bool hy = iy < ny - 1;
     float b[3] = {0.f, 0.f, 0.f}, qn[3] = {0.f, 0.f, 0.f};
     const float xc = st[me];
@@ -176,13 +176,18 @@ __global__ void __launch_bounds__(512) k_prior(DevGeom g, PriorArgs a, int cols,
 cudaError_t launch_prior(const DevGeom& g, const PriorArgs& a, cudaStream_t s) {
   const int zw = (g.nz + 31) / 32;
   if (zw > 16) return cudaErrorInvalidValue;
+  // default: up to 8 columns per block (7 owned + 1 halo; at most 32 warps), and enough row
+  // chunks for about one block per SM (the blocks are large: one wave, no tail)
   const int cols = g.tune[SPDHG_TUNE_PRIOR_COLS] ? g.tune[SPDHG_TUNE_PRIOR_COLS]
-                                                 : std::max(2, std::min(16 / zw, g.nx + 1));
-  const int ychunk = g.tune[SPDHG_TUNE_PRIOR_YCHUNK] ? g.tune[SPDHG_TUNE_PRIOR_YCHUNK] : 64;
-  if (cols * zw > 16) return cudaErrorInvalidValue;
+                                                 : std::max(2, std::min(std::min(8, 32 / zw), g.nx + 1));
+  const int gx = (g.nx + cols - 2) / (cols - 1);
+  const int chunks = std::max(1, std::min(g.ny, 152 / gx));
+  const int ychunk = g.tune[SPDHG_TUNE_PRIOR_YCHUNK] ? g.tune[SPDHG_TUNE_PRIOR_YCHUNK] : (g.ny + chunks - 1) / chunks;
+  const int stages = g.tune[SPDHG_TUNE_PRIOR_STAGES] ? g.tune[SPDHG_TUNE_PRIOR_STAGES] : 4;
+  if (cols * zw > 32 || (stages != 3 && stages != 4)) return cudaErrorInvalidValue;
   const int zc = zw * 32;
   const size_t stage = (size_t)2 * (cols + 1) * zc + (size_t)5 * cols * zc;
-  const size_t smem = (kPriorStages * stage + 2 * (size_t)cols * zc) * sizeof(float);
+  const size_t smem = (stages * stage + 2 * (size_t)cols * zc) * sizeof(float);
   dim3 grid((g.nx + cols - 2) / (cols - 1), (g.ny + ychunk - 1) / ychunk);
   const int threads = cols * zw * 32;
   auto launch = [&](auto kern) -> cudaError_t {
@@ -191,10 +196,11 @@ cudaError_t launch_prior(const DevGeom& g, const PriorArgs& a, cudaStream_t s) {
     kern<<<grid, threads, smem, s>>>(g, a, cols, ychunk);
     return cudaGetLastError();
   };
+  const bool s3 = stages == 3;
   switch (a.kind) {
-    case SPDHG_PRIOR_TV: return launch(k_prior<SPDHG_PRIOR_TV>);
-    case SPDHG_PRIOR_DTV: return launch(k_prior<SPDHG_PRIOR_DTV>);
-    case SPDHG_PRIOR_ATV: return launch(k_prior<SPDHG_PRIOR_ATV>);
+    case SPDHG_PRIOR_TV: return s3 ? launch(k_prior<SPDHG_PRIOR_TV, 3>) : launch(k_prior<SPDHG_PRIOR_TV, 4>);
+    case SPDHG_PRIOR_DTV: return s3 ? launch(k_prior<SPDHG_PRIOR_DTV, 3>) : launch(k_prior<SPDHG_PRIOR_DTV, 4>);
+    case SPDHG_PRIOR_ATV: return s3 ? launch(k_prior<SPDHG_PRIOR_ATV, 3>) : launch(k_prior<SPDHG_PRIOR_ATV, 4>);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -131,8 +131,11 @@ extern "C" int spdhg_autotune(spdhg_ctx* ctx, int reps, int* chosen, void* strea
   }
   if (stencil) {
     Knob c{SPDHG_TUNE_PRIOR_COLS, false, {}};
-    for (int v = 2; v * zw <= 16; v = v < 4 ? v + 1 : v * 2) c.values.push_back(v);
+    for (int v : {2, 3, 4, 6, 8, 12, 16, 32})
+      if (v * zw <= 32 && v <= g.nx + 1) c.values.push_back(v);
     knobs.push_back(c);
+    Knob st{SPDHG_TUNE_PRIOR_STAGES, false, {3, 4}};
+    knobs.push_back(st);
     Knob y{SPDHG_TUNE_PRIOR_YCHUNK, false, {}};
     for (int v : {16, 32, 64, 128, 256})
       if (v / 2 < g.ny) y.values.push_back(v);

@@ -167,7 +167,8 @@ def test_autotune_keeps_state_and_parity(kind):
         assert chosen["fwd_warps"] in (0, 4, 8, 16)
         assert chosen["fwd_split"] in (0, 1, 2, 4, 8)
         if kind == "dtv":
-            assert 2 <= chosen["prior_cols"] <= 16 and chosen["prior_ychunk"] in (16, 32, 64, 128, 256)
+            assert 2 <= chosen["prior_cols"] <= 32 and chosen["prior_ychunk"] in (16, 32, 64, 128, 256)
+            assert chosen["prior_stages"] in (3, 4)
         ctx.spdhg_iterate(seq[10:])
         x = torch.zeros(sc.n_voxels, device="cuda")
         ctx.spdhg_get("x", x)
