@@ -86,7 +86,9 @@ typedef struct {
   double dtv_eta_frac;        /* dTV: xi = grad v / sqrt(|grad v|^2 + eta^2), eta = frac*max|grad v| */
   int sampling;               /* SPDHG_SAMPLING_*: balanced = prior w.p. 1/2 (Sec. 4.2) */
   int precond;                /* 1: Eq. EQU:STEPSIZE:PRECOND for data blocks; 0: scalar Eq.
-                                 EQU:STEPSIZE:SCALAR with ||P_i|| by power iteration */
+                                 EQU:STEPSIZE:SCALAR with ||P_i|| by power iteration on P_i^T P_i
+                                 from the constant vector, until the eigenvalue changes by less than
+                                 1e-7 (relative) over 10 steps (at most 2000 steps) */
   double rho;                 /* < 1 (Theorem "Step Size Parameters"); 0.99 if <= 0 */
   double gamma;               /* > 0; 1 if <= 0 (Sec. 4: gamma = 1) */
   uint64_t seed;              /* sampler seed (spdhg_run) */

@@ -186,6 +186,51 @@ int prepare_forward(spdhg_ctx* ctx, int subset, FwdArgs& a, cudaStream_t s) {
   return SPDHG_OK;
 }
 
+// ||P_i|| by power iteration on P_i^T P_i (scalar step sizes, Eq. EQU:STEPSIZE:SCALAR): P_i is
+// non-negative, so the iteration from the constant unit vector converges to its Perron vector.
+// The eigenvalue estimate is read every kNormCheck steps; the iteration stops once it changes by
+// less than kNormTol (relative) over those steps, or after kNormMax steps.  FP64 norms, the
+// normalisation done on the device.  Uses x[1], tmp_img, tmp_sino and wdy as scratch (before
+// spdhg_setup writes the initial state).
+constexpr int kNormCheck = 10, kNormMax = 2000;
+constexpr double kNormTol = 1e-7;
+
+int subset_norm(spdhg_ctx* ctx, int i, cudaStream_t s, double* out) {
+  const int64_t N = ctx->N;
+  float* v = ctx->x[1];
+  float* y = ctx->tmp_img;
+  const float* mult = ctx->has_mult ? ctx->mult : nullptr;
+  k_fill<<<grid_for(N), 256, 0, s>>>(v, N, (float)(1.0 / sqrt((double)N)));
+  CK(cudaGetLastError());
+  double prev = -1.0, ss = 0.0;
+  for (int it = 0; it < kNormMax; ++it) {
+    FwdArgs fa{};
+    fa.x = v;
+    fa.out = ctx->tmp_sino;
+    fa.mult = mult;
+    if (int st = prepare_forward(ctx, i, fa, s)) return st;
+    CK(launch_forward(ctx->dg, i, FWD_PROJECT, fa, s));
+    CK(launch_gather_subset(ctx->dg, i, ctx->tmp_sino, mult, ctx->wdy, s));
+    BwdArgs ba{};
+    ba.w = ctx->wdy;
+    ba.out = y;
+    CK(launch_backward(ctx->dg, i, BWD_OUT, ba, s));
+    CK(launch_sumsq(y, N, ctx->red, ctx->red_blocks, ctx->red_out + 3, s));
+    CK(launch_normalize(y, N, ctx->red_out + 3, v, s));
+    if ((it + 1) % kNormCheck == 0) {
+      CK(cudaMemcpyAsync(&ss, ctx->red_out + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      const double lam = sqrt(ss);  // ||P^T P v|| with ||v|| = 1: the largest eigenvalue of P^T P
+      if (prev > 0.0 && fabs(lam - prev) <= kNormTol * lam) break;
+      prev = lam;
+    }
+  }
+  CK(cudaMemcpyAsync(&ss, ctx->red_out + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  *out = sqrt(sqrt(ss));
+  return SPDHG_OK;
+}
+
 }  // namespace
 
 // Enqueues the kernels of one SPDHG iteration (Algorithm 2) on block i and advances the
@@ -608,7 +653,6 @@ int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int
   if (p.prior == SPDHG_PRIOR_DTV && !(p.dtv_gamma >= 0.0 && p.dtv_gamma < 1.0)) return fail(ctx, SPDHG_ERR_ARG, "dtv_gamma must be in [0, 1)");
   if (p.prior == SPDHG_PRIOR_TGV ? !(p.alpha0 > 0 && p.alpha1 > 0) : (p.prior != SPDHG_PRIOR_NONE && !(p.alpha > 0)))
     return fail(ctx, SPDHG_ERR_ARG, "prior weights must be positive");
-  if (!p.precond) return fail(ctx, SPDHG_ERR_UNSUPPORTED, "scalar data step sizes are not available; use precond = 1");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t N = ctx->N, M = ctx->M;
   const int m = ctx->geom.n_subsets;
@@ -637,10 +681,28 @@ int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int
   ctx->probs = block_probs(m, p.prior, p.sampling);
   const double gn = grad_norm(ctx->geom.nx, ctx->geom.ny, ctx->geom.nz);
 
+  // scalar data steps (Eq. EQU:STEPSIZE:SCALAR): sigma_i = gamma rho / ||P_i||, T_i = rho p_i /
+  // (gamma ||P_i||), with ||P_i|| by power iteration
+  std::vector<double> norms;
+  if (!p.precond) {
+    CK(dalloc(&ctx->tmp_sino, M));
+    CK(dalloc(&ctx->tmp_img, N));
+    double t_data = INFINITY;
+    for (int i = 0; i < m; ++i) {
+      double nrm = 0.0;
+      if (int st = subset_norm(ctx, i, s, &nrm)) return st;
+      norms.push_back(nrm);
+      if (nrm > 0.0) t_data = std::min(t_data, p.rho * ctx->probs[i] / (p.gamma * nrm));
+    }
+    k_fill<<<grid_for(N), 256, 0, s>>>(ctx->T, N, (float)t_data);
+    CK(cudaGetLastError());
+  }
   // T = min over data blocks of rho p_i / (gamma P_i^T 1)  (Eq. EQU:STEPSIZE:PRECOND)
-  k_fill<<<grid_for(N), 256, 0, s>>>(ctx->T, N, INFINITY);
-  CK(cudaGetLastError());
-  for (int i = 0; i < m; ++i) {
+  if (p.precond) {
+    k_fill<<<grid_for(N), 256, 0, s>>>(ctx->T, N, INFINITY);
+    CK(cudaGetLastError());
+  }
+  for (int i = 0; i < (p.precond ? m : 0); ++i) {
     if (ctx->has_mult) {
       CK(launch_gather_subset(ctx->dg, i, ctx->mult, nullptr, ctx->wdy, s));
     } else {
@@ -668,8 +730,16 @@ int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int
   }
   k_finalize_T<<<grid_for(N), 256, 0, s>>>(ctx->T, N, t_prior);
   CK(cudaGetLastError());
-  // sigma_j = gamma rho / (P 1)_j for every bin (Eq. EQU:STEPSIZE:PRECOND), stored once
-  {
+  // sigma_j = gamma rho / (P 1)_j for every bin (Eq. EQU:STEPSIZE:PRECOND), stored once; scalar
+  // steps: gamma rho / ||P_i|| on every bin of subset i
+  if (!p.precond) {
+    const int64_t RP = (int64_t)ctx->dg.R * ctx->dg.P;
+    for (int v = 0; v < ctx->dg.V; ++v) {
+      const double nrm = norms[v % m];
+      k_fill<<<grid_for(RP), 256, 0, s>>>(ctx->sigma + v * RP, RP, nrm > 0.0 ? (float)(p.gamma * p.rho / nrm) : 0.f);
+    }
+    CK(cudaGetLastError());
+  } else {
     FwdArgs a{};
     a.x = ctx->x[0];  // unused by the sigma pass
     a.out = ctx->sigma;

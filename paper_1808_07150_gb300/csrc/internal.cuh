@@ -150,6 +150,9 @@ cudaError_t launch_prior_term(const DevGeom& g, int kind, const float* x, const 
                               int nblocks, double* out, cudaStream_t s);
 cudaError_t launch_side_max_grad(const DevGeom& g, const float* side, double* partial, int nblocks,
                                  double* out, cudaStream_t s);
+// *out = sum_j v_j^2 (FP64, deterministic);  v = y / sqrt(*ss)
+cudaError_t launch_sumsq(const float* v, int64_t n, double* partial, int nblocks, double* out, cudaStream_t s);
+cudaError_t launch_normalize(const float* y, int64_t n, const double* ss, float* v, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------
 // iteration driver (api.cu) and epoch graphs (graph.cu)

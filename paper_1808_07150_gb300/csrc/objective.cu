@@ -57,6 +57,39 @@ __global__ void k_data_term(const float* __restrict__ ax, const float* __restric
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// sum of squares (FP64) of v, for the power iteration of the operator norms
+__global__ void k_sumsq(const float* __restrict__ v, int64_t n, double* partial) {
+  __shared__ double sh[256];
+  double acc = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double a = v[j];
+    acc += a * a;
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// v = y / sqrt(*ss)  (v = 0 if the norm is 0)
+__global__ void k_normalize(const float* __restrict__ y, int64_t n, const double* __restrict__ ss, float* __restrict__ v) {
+  const double q = *ss;
+  const float inv = q > 0.0 ? (float)(1.0 / sqrt(q)) : 0.f;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    v[j] = y[j] * inv;
+}
+
+cudaError_t launch_sumsq(const float* v, int64_t n, double* partial, int nblocks, double* out, cudaStream_t s) {
+  k_sumsq<<<nblocks, 256, 0, s>>>(v, n, partial);
+  k_finish_sum<<<1, 256, 0, s>>>(partial, nblocks, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normalize(const float* y, int64_t n, const double* ss, float* v, cudaStream_t s) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  k_normalize<<<(int)b, 256, 0, s>>>(y, n, ss, v);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_data_term(const float* ax, const float* b, const float* r, int64_t M,
                              double* partial, int nblocks, double* out, cudaStream_t s) {
   k_data_term<<<nblocks, 256, 0, s>>>(ax, b, r, M, partial);

@@ -155,3 +155,37 @@ def test_invalid_inputs_are_rejected():
         import torch
         with pytest.raises(pkg.SpdhgError):
             ctx.spdhg_project(torch.zeros(sc.n_voxels, device="cuda"), torch.zeros(sc.n_bins, device="cuda"), sc.n_subsets)
+
+
+@pytest.mark.parametrize("sc", [synth.tiny_3d(steep=True), synth.config_2d()], ids=lambda s: s.name)
+def test_scalar_step_sizes_and_iterations_match_oracle(sc):
+    """precond = 0 (Eq. EQU:STEPSIZE:SCALAR): sigma_i = gamma rho / ||P_i|| on the bins of subset i,
+    T = min_i rho p_i / (gamma ||P_i||) and the prior's scalar step.  The norms come from power
+    iteration on both sides (the oracle runs 3000 steps); then 40 SPDHG iterations."""
+    import torch
+    import paper_1808_07150_gb300 as pkg
+    d, prob = problem(sc)
+    prior = _prior("tv", None)
+    probs = O.probabilities(sc.n_subsets, prior)
+    norms = []
+    for i in range(sc.n_subsets):
+        mask = O.subset_mask(sc, i)
+        norms.append(O.operator_norm_power(lambda x: O.project(sc, x, i, prob.mult),
+                                           lambda y: O.backproject(sc, y * mask, i, prob.mult),
+                                           sc.image_shape, iters=3000))
+    steps = O.step_sizes(sc, prob.mult, prior, probs, precond=False, data_norms=norms)
+    seq = O.sample(4321, 40, probs)
+    params = pkg.make_params("tv", alpha=0.08, precond=False)
+    with pkg.Context(sc) as ctx:
+        upload(ctx, d)
+        ctx.spdhg_setup(params, None)
+        g = _gpu_state(ctx, sc, ["T"])
+        sig = torch.zeros(sc.n_bins, device="cuda")
+        ctx.spdhg_get("sigma", sig)
+        assert rel(host(sig), steps["sigma"]) < 1e-5
+        assert rel(g["T"], steps["T"]) < 1e-5
+        ctx.spdhg_iterate(seq)
+        g = _gpu_state(ctx, sc, ["x", "y"])
+    st, steps_o = O.spdhg(prob, prior, seq, probs, steps=steps)
+    assert rel(g["x"], O.next_primal(st, steps_o)) < 1e-4
+    assert rel(g["y"], st.y) < 1e-4
