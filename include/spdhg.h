@@ -165,6 +165,17 @@ int spdhg_get(spdhg_ctx* ctx, int what, void* dst, int where, void* stream);
  * iteration.  Requires spdhg_setup. */
 int spdhg_set(spdhg_ctx* ctx, int what, const void* src, int where, void* stream);
 
+/* Checkpoint files.  spdhg_save_state writes the iteration state (x, z, y, the prior duals and
+ * for TGV w, zw and the second dual; not T or sigma, which follow from the data and parameters),
+ * the problem sizes, the parameters that define the iteration and the iteration count.
+ * spdhg_load_state reads such a file into a context that has the same data sizes and was set up
+ * with the same parameters (run length, objective cadence, sampler seed and launch mode may
+ * differ); it fails with SPDHG_ERR_STATE otherwise and SPDHG_ERR_DATA for a file that is not a
+ * state file or is truncated (a truncated file may leave the state partly overwritten).  Both
+ * synchronise the device. */
+int spdhg_save_state(spdhg_ctx* ctx, const char* path);
+int spdhg_load_state(spdhg_ctx* ctx, const char* path);
+
 /* Psi(x) in FP64 (Problem "PET Reconstruction with Subsets"): out[0] = sum_j varphi_j((P x)_j)
  * (Eq. EQU:LOCALDISTANCE), out[1] = alpha R(x) for the prior of the last spdhg_setup (0 if none),
  * out[2] = out[0] + out[1].  x = NULL uses the context's current iterate (and w for TGV). */

@@ -135,6 +135,12 @@ class Context:
         ps = _capi.pointer(src, numel)
         self._check(_capi.lib().spdhg_set(self.h, code, ps[0], ps[1], _stream(stream)))
 
+    def spdhg_save_state(self, path):
+        self._check(_capi.lib().spdhg_save_state(self.h, str(path).encode()))
+
+    def spdhg_load_state(self, path):
+        self._check(_capi.lib().spdhg_load_state(self.h, str(path).encode()))
+
     def spdhg_objective(self, x=None, stream=None):
         px = _capi.pointer(x, self.n_voxels)
         out = (ctypes.c_double * 3)()

@@ -25,7 +25,7 @@ _EXPORTS = [
     "spdhg_project", "spdhg_backproject", "spdhg_setup", "spdhg_iterate", "spdhg_get",
     "spdhg_objective", "spdhg_probabilities", "spdhg_sample", "spdhg_run", "spdhg_profile",
     "spdhg_profile_read", "spdhg_backproject_noalloc", "spdhg_tune", "spdhg_autotune",
-    "spdhg_run_batch", "spdhg_set",
+    "spdhg_run_batch", "spdhg_set", "spdhg_save_state", "spdhg_load_state",
     "unet_gemm", "unet_device_error", "unet_create", "unet_destroy", "unet_last_error", "unet_num_params",
     "unet_set_params", "unet_init", "unet_get_params", "unet_get_grads", "unet_forward", "unet_backward", "unet_adam_step",
 ]
@@ -98,6 +98,8 @@ def lib():
             "spdhg_iterate": ([vp, P(ctypes.c_int32), i32, vp], i32),
             "spdhg_get": ([vp, i32, vp, i32, vp], i32),
             "spdhg_set": ([vp, i32, vp, i32, vp], i32),
+            "spdhg_save_state": ([vp, ctypes.c_char_p], i32),
+            "spdhg_load_state": ([vp, ctypes.c_char_p], i32),
             "spdhg_objective": ([vp, vp, i32, P(dp), vp], i32),
             "spdhg_probabilities": ([vp, P(dp), P(i32)], i32),
             "spdhg_sample": ([u64, u64, i32, P(dp), i32, P(ctypes.c_int32)], i32),

@@ -124,3 +124,30 @@ def test_learned_warm_start_gains_over_zero_start():
             c.close()
     assert np.mean(gains_img) < 0.8, gains_img      # x0 closer to x* than x_k
     assert np.mean(gains_gap) < 1.0, gains_gap      # smaller gap after the same epochs
+
+
+@pytest.mark.parametrize("kind", ["tv", "tgv"])
+def test_state_file_resume_is_bit_identical(tmp_path, kind):
+    """spdhg_save_state after 2 epochs, spdhg_load_state into a fresh context set up alike: the
+    next 2 epochs are bit-identical; a file written with other parameters is refused."""
+    import paper_1808_07150_gb300 as pkg
+    from paper_1808_07150_gb300 import warmstart as W
+    sc = synth.config_3d_small()
+    d, _ = problem(sc, seed=23, counts=1e5)
+    params = pkg.make_params(kind, alpha=0.05, alpha0=0.2, alpha1=0.1, seed=7)
+    path = tmp_path / "state.bin"
+    with pkg.Context(sc) as a, pkg.Context(sc) as b:
+        for c in (a, b):
+            upload(c, d)
+            c.spdhg_setup(params, None)
+        W.run_epochs(a, params, 2, 0)
+        a.spdhg_save_state(path)
+        oa, _ = W.run_epochs(a, params, 2, 2)
+        b.spdhg_load_state(path)
+        ob, _ = W.run_epochs(b, params, 2, 2)
+        xa, xb = _state(a, sc, ["x"])["x"], _state(b, sc, ["x"])["x"]
+        b.spdhg_setup(pkg.make_params(kind, alpha=0.07, alpha0=0.3, alpha1=0.1, seed=7), None)
+        with pytest.raises(pkg.SpdhgError):
+            b.spdhg_load_state(path)
+    np.testing.assert_array_equal(oa, ob)
+    np.testing.assert_array_equal(host(xa), host(xb))
