@@ -342,6 +342,142 @@ cudaError_t launch(int am, int bm, int em, const GemmArgs& g, dim3 grid, cudaStr
   return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------------------------------------------------------
+// 3x3x3 convolution for small channel counts without the im2col gather.
+//
+// A CTA owns 16 consecutive x positions x 8 consecutive z slices at one y: 128 output rows, row
+// r = 8 m + j <-> voxel (y, x0 + m, z0 + j).  It stages the input halo (3 y x 18 x x 10 z voxels)
+// once, as one plane per 8-channel group with voxel (dy, xx, zz) at ((dy * 18 + xx) * 10 + zz) * 16
+// bytes, and all 27 taps' weights.  For tap (dy, dx, dz) the A operand of the MMA is the same halo
+// read from a shifted start: core matrix m (rows 8 m .. 8 m + 7, the z-run at x0 + m) starts at
+// ((dy * 18 + m + dx) * 10 + dz) * 16, i.e. consecutive core matrices are 160 bytes apart (SBO)
+// and the two channel groups of a K = 16 step one plane apart (LBO).  So a tap costs one MMA per
+// 16 channels and no copies; padding is the zero fill of the halo outside the volume.
+// ------------------------------------------------------------------------------------------
+
+constexpr int HX = 18, HZ = 10, HROWS = 3 * HX * HZ;  // halo voxels
+
+bool halo_fits(const GemmArgs& g) {
+  if (g.a_c != 16 && g.a_c != 32) return false;
+  if (g.N < 16 || g.N > 64 || (g.N & 15) || (g.nx & 15) || (g.nz & 7)) return false;
+  const size_t halo = (size_t)HROWS * g.a_c * 2, wts = (size_t)g.N * 27 * g.a_c * 2;
+  return halo + wts <= 110 * 1024;
+}
+
+template <int EM>
+__global__ void __launch_bounds__(THREADS) k_conv3_halo(GemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int x0 = blockIdx.x * 16, y = blockIdx.y, z0 = blockIdx.z * 8;
+  const int cg8 = g.a_c >> 3;                        // channel groups of the input
+  const uint32_t plane = (uint32_t)HROWS * 16;       // bytes per channel-group plane of the halo
+  const uint32_t sh = umma::smem_u32(smem);
+  const uint32_t sb = sh + ((cg8 * plane + 1023) & ~1023u);  // weights after the halo
+  const int K = 27 * g.a_c;
+  uint32_t ncols = 32;
+  while ((int)ncols < g.N) ncols <<= 1;
+
+  if (warp == 0) umma::tmem_alloc(&tmem_slot, ncols);
+  if (tid == 0) {
+    umma::mbar_init(&mbar, 1);
+    umma::fence_mbar_init();
+  }
+  // halo: HROWS voxels x cg8 chunks, zero outside the volume
+  for (int idx = tid; idx < HROWS * cg8; idx += THREADS) {
+    const int cg = idx / HROWS, h = idx - cg * HROWS;
+    const int dyi = h / (HX * HZ), rem = h - dyi * (HX * HZ), xx = rem / HZ, zz = rem - xx * HZ;
+    const int yy = y + dyi - 1, xg = x0 + xx - 1, zg = z0 + zz - 1;
+    const bool ok = yy >= 0 && yy < g.ny && xg >= 0 && xg < g.nx && zg >= 0 && zg < g.nz;
+    const __nv_bfloat16* src = ok ? g.a + ((size_t)(yy * g.nx + xg) * g.nz + zg) * g.a_stride + g.a_off + cg * 8 : g.a;
+    umma::cp16(sh + cg * plane + h * 16, src, ok ? 16u : 0u);
+  }
+  // weights B[n][k], k = tap * a_c + c, K-major core layout: core (row block rb, k block kb)
+  for (int idx = tid; idx < g.N * (K >> 3); idx += THREADS) {
+    const int n = idx % g.N, kb = idx / g.N;
+    umma::cp16(sb + ((n >> 3) * (K >> 3) + kb) * 128 + (n & 7) * 16, g.b + (size_t)n * g.b_stride + kb * 8, 16u);
+  }
+  umma::cp_commit_wait_all();
+  umma::fence_proxy_async_smem();
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = tmem_slot;
+  if (tid == 0) {
+    const uint32_t idesc = umma::idesc_bf16(BM, g.N, false, false);
+    const uint32_t b_sbo = (uint32_t)(K >> 3) * 128;  // next row block of 8 weights rows
+    int step = 0;
+    for (int tap = 0; tap < 27; ++tap) {
+      const int dy = tap / 9, dx = (tap / 3) % 3, dz = tap % 3;
+      for (int c16 = 0; c16 < (g.a_c >> 4); ++c16) {
+        const uint32_t a0 = sh + 2 * c16 * plane + (uint32_t)((dy * HX + dx) * HZ + dz) * 16;
+        const uint64_t ad = umma::smem_desc(a0, plane, HZ * 16);
+        const uint64_t bd = umma::smem_desc(sb + (uint32_t)(tap * cg8 + 2 * c16) * 128, 128, b_sbo);
+        umma::mma_bf16(tmem, ad, bd, idesc, step > 0 ? 1u : 0u);
+        ++step;
+      }
+    }
+    umma::commit(&mbar);
+  }
+  const bool ok = umma::mbar_wait(&mbar, 0, WAIT_CYCLES);
+  const bool failed = __syncthreads_or(!ok);
+  if (failed) {
+    set_error(2);
+    const long long t0 = clock64();
+    while (clock64() - t0 < 2000000ll) {
+    }
+  }
+  umma::fence_after_sync();
+  // epilogue: row r = tid <-> voxel (y, x0 + r / 8, z0 + r % 8)
+  const size_t orow = ((size_t)y * g.nx + x0 + (tid >> 3)) * g.nz + z0 + (tid & 7);
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  for (int n0 = 0; n0 < g.N; n0 += 8) {
+    float v[8];
+    umma::tmem_ld8(trow + n0, v);
+    if (failed) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      if (g.bias) v[j] += g.bias[n0 + j];
+      if (g.relu) v[j] = fmaxf(v[j], 0.f);
+    }
+    if (g.mask) {
+      const __nv_bfloat16* mk = g.mask + orow * g.mask_stride + g.mask_off + n0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (n0 + j >= g.mask_from && !(__bfloat162float(mk[j]) > 0.f)) v[j] = 0.f;
+    }
+    if (EM == E_F32) {
+      float* dst = g.outf + orow * g.N + n0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) dst[j] = v[j];
+    } else {
+      __align__(16) __nv_bfloat162 h2[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+      *reinterpret_cast<uint4*>(g.out + orow * g.out_stride + g.out_off + n0) = *reinterpret_cast<uint4*>(h2);
+    }
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, ncols);
+}
+
+cudaError_t launch_conv3_halo(int em, const GemmArgs& g, cudaStream_t s) {
+  if (!halo_fits(g) || g.M != g.ny * g.nx * g.nz || g.K != 27 * g.a_c || g.out_child) return cudaErrorNotSupported;
+  const size_t smem = (((size_t)(g.a_c >> 3) * HROWS * 16 + 1023) & ~(size_t)1023) + (size_t)g.N * 27 * g.a_c * 2 + 1024;
+  const dim3 grid(g.nx / 16, g.ny, g.nz / 8);
+  auto go = [&](auto kern) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, THREADS, smem, s>>>(g);
+    return cudaGetLastError();
+  };
+  if (em == E_BF16) return go(k_conv3_halo<E_BF16>);
+  if (em == E_F32) return go(k_conv3_halo<E_F32>);
+  return cudaErrorInvalidValue;
+}
+
 int read_error(cudaStream_t s) {
   int h = 0;
   if (cudaMemcpyFromSymbolAsync(&h, g_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;

@@ -47,6 +47,10 @@ struct GemmArgs {
 };
 
 cudaError_t launch(int am, int bm, int em, const GemmArgs& g, dim3 grid, cudaStream_t s);
+// 3x3x3 convolution (A_CONV3 operands, B = weights [N][27 a_c]) from a staged input halo with the
+// taps as shifted shared-memory descriptors; cudaErrorNotSupported when the shape does not fit
+// (a_c in {16, 32}, N <= 64, nx % 16 == 0, nz % 8 == 0), in which case launch() serves it
+cudaError_t launch_conv3_halo(int em, const GemmArgs& g, cudaStream_t s);
 // first failure code recorded by any launch (0: none); synchronises s
 int read_error(cudaStream_t s);
 

@@ -372,6 +372,15 @@ struct View {
   int stride, off, c;
 };
 
+// 3x3x3 convolution pass: the halo kernel where the shape allows it, else the gather kernel
+int conv3_launch(unet_net* net, const ig::GemmArgs& a, cudaStream_t s) {
+  cudaError_t e = ig::launch_conv3_halo(ig::E_BF16, a, s);
+  if (e == cudaErrorNotSupported)  // returned before any CUDA call: the shape does not fit
+    e = ig::launch(ig::A_CONV3, ig::B_GEMM_K, ig::E_BF16, a, dim3((a.M + 127) / 128), s);
+  UCK(e);
+  return UNET_OK;
+}
+
 int conv3_fwd(unet_net* net, int l, const Param& pr, View x, bf16* out, int o_stride, int o_off, cudaStream_t s) {
   ig::GemmArgs a{};
   a.M = (int)net->V[l];
@@ -383,8 +392,7 @@ int conv3_fwd(unet_net* net, int l, const Param& pr, View x, bf16* out, int o_st
   a.bias = net->w + pr.off_b;
   a.relu = 1;
   a.out = out; a.out_stride = o_stride; a.out_off = o_off;
-  UCK(ig::launch(ig::A_CONV3, ig::B_GEMM_K, ig::E_BF16, a, dim3((a.M + 127) / 128), s));
-  return UNET_OK;
+  return conv3_launch(net, a, s);
 }
 
 // dX = conv3^T(G) masked by (mask > 0) on columns >= mask_from
@@ -399,8 +407,7 @@ int conv3_bwd_data(unet_net* net, int l, const Param& pr, View gv, bf16* out, in
   a.ny = net->ny[l]; a.nx = net->nx[l]; a.nz = net->nz[l];
   a.out = out; a.out_stride = o_stride; a.out_off = o_off;
   a.mask = mask.p; a.mask_stride = mask.stride; a.mask_off = mask.off; a.mask_from = mask_from;
-  UCK(ig::launch(ig::A_CONV3, ig::B_GEMM_K, ig::E_BF16, a, dim3((a.M + 127) / 128), s));
-  return UNET_OK;
+  return conv3_launch(net, a, s);
 }
 
 int ensure_part(unet_net* net, size_t n) {
