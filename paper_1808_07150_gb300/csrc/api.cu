@@ -291,6 +291,7 @@ int spdhg::enqueue_block(spdhg_ctx* ctx, int i, cudaStream_t s) {
     ta.Tw = ctx->Tw;
     ta.sigma = ctx->sigma_prior[kblk];
     ta.inv_p = inv_p;
+    ta.bscr = ctx->tgv_b;
     {
       ProfScope ps(ctx, SPDHG_KERNEL_TGV, s);
       CK(launch_tgv(ctx->dg, ta, s));
@@ -512,7 +513,7 @@ void spdhg_destroy(spdhg_ctx* ctx) {
   if (!ctx) return;
   void* ptrs[] = {ctx->d_view, ctx->d_view_inv, ctx->d_rad, ctx->d_rs, ctx->d_runs, ctx->d_seg, ctx->d_plane_seg, ctx->b, ctx->r, ctx->mult, ctx->side,
                   ctx->x[0], ctx->x[1], ctx->z, ctx->T, ctx->y, ctx->sigma, ctx->wdy, ctx->q[0], ctx->q[1],
-                  ctx->w[0], ctx->w[1], ctx->zw, ctx->q2[0], ctx->q2[1], ctx->tmp_sino, ctx->tmp_img, ctx->fwd_part, ctx->fwd_tickets,
+                  ctx->w[0], ctx->w[1], ctx->zw, ctx->q2[0], ctx->q2[1], ctx->tgv_b, ctx->tmp_sino, ctx->tmp_img, ctx->fwd_part, ctx->fwd_tickets,
                   ctx->red, ctx->red_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -673,6 +674,7 @@ int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int
     CK(dalloc(&ctx->w[0], 3 * N));
     CK(dalloc(&ctx->w[1], 3 * N));
     CK(dalloc(&ctx->zw, 3 * N));
+    CK(dalloc(&ctx->tgv_b, 6 * N));
     CK(dalloc(&ctx->q2[0], 6 * N));
     CK(dalloc(&ctx->q2[1], 6 * N));
   }

@@ -3,7 +3,7 @@
 // The sampled block sequence changes every epoch (Algorithm 2 draws i_k at random), so the
 // graph has a fixed topology and the sequence is written into it from the host:
 //   * each iteration of each reconstruction owns a fixed set of kernel-node "slots" (forward,
-//     backward, [w step,] prior), chained in iteration order; the reconstructions are
+//     backward, [w step,] prior [, second prior pass for TGV]), chained in iteration order; the reconstructions are
 //     independent branches of the same graph, so small problems run side by side on the SMs;
 //   * the kernels of one iteration on block i (with the current ping-pong parities of x, q, w)
 //     are captured once from the eager launch path (enqueue_block) into a small template graph;
@@ -28,7 +28,7 @@ namespace spdhg {
 
 namespace {
 
-enum Slot { SLOT_FWD = 0, SLOT_BWD = 1, SLOT_WSTEP = 2, SLOT_PRIOR = 3, SLOT_KINDS = 4 };
+enum Slot { SLOT_FWD = 0, SLOT_BWD = 1, SLOT_WSTEP = 2, SLOT_PRIOR = 3, SLOT_PRIOR2 = 4, SLOT_KINDS = 5 };
 
 int fail(spdhg_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -96,6 +96,7 @@ int n_slots(const spdhg_ctx* c, int* slots) {
   slots[n++] = SLOT_BWD;
   if (c->params.prior == SPDHG_PRIOR_TGV) slots[n++] = SLOT_WSTEP;
   if (c->params.prior != SPDHG_PRIOR_NONE) slots[n++] = SLOT_PRIOR;
+  if (c->params.prior == SPDHG_PRIOR_TGV) slots[n++] = SLOT_PRIOR2;  // TGV: dual pass + primal pass
   return n;
 }
 
@@ -132,7 +133,8 @@ int capture(spdhg_ctx* ctx, int i, int par, Template& t) {
   t.par_xor = par ^ par_after;
   // walk the captured chain from its root
   const bool data = i < ctx->geom.n_subsets;
-  const int expect = data ? (ctx->params.prior == SPDHG_PRIOR_TGV ? 3 : 2) : 1;
+  const bool tgv = ctx->params.prior == SPDHG_PRIOR_TGV;
+  const int expect = data ? (tgv ? 3 : 2) : (tgv ? 2 : 1);
   static const int data_slots[3] = {SLOT_FWD, SLOT_BWD, SLOT_WSTEP};
   cudaGraphNode_t node = nullptr;
   size_t nn = 1;
@@ -145,7 +147,7 @@ int capture(spdhg_ctx* ctx, int i, int par, Template& t) {
     GCK(ctx, cudaGraphNodeGetType(node, &ty));
     if (ty != cudaGraphNodeTypeKernel) return fail(ctx, SPDHG_ERR_STATE, "captured iteration holds a non-kernel node");
     GCK(ctx, cudaGraphKernelNodeGetParams(node, &t.p[k]));
-    t.slot[k] = data ? data_slots[k] : SLOT_PRIOR;
+    t.slot[k] = data ? data_slots[k] : (k == 0 ? SLOT_PRIOR : SLOT_PRIOR2);
     if (k + 1 < expect) {
       size_t nd = 1;
       cudaGraphNode_t next = nullptr;
@@ -209,15 +211,17 @@ int build(EpochGraph& eg, spdhg_ctx* err_ctx) {
     b.nslot = n_slots(ctx, b.slots);
     // placeholder parameters of each slot: any template holding that slot
     cudaKernelNodeParams init[SLOT_KINDS];
-    bool have[SLOT_KINDS] = {false, false, false, false};
+    bool have[SLOT_KINDS] = {false, false, false, false, false};
     const Template* t = nullptr;
     const int par = parity_of(ctx);
     if (int st = get_template(ctx, 0, par, &t)) return st;
     for (int k = 0; k < t->n; ++k) { init[t->slot[k]] = t->p[k]; have[t->slot[k]] = true; }
     if (ctx->params.prior != SPDHG_PRIOR_NONE) {
       if (int st = get_template(ctx, ctx->geom.n_subsets, par, &t)) return st;
-      init[SLOT_PRIOR] = t->p[0];
-      have[SLOT_PRIOR] = true;
+      for (int k = 0; k < t->n; ++k) {
+        init[t->slot[k]] = t->p[k];
+        have[t->slot[k]] = true;
+      }
     }
     for (int j = 0; j < b.nslot; ++j)
       if (!have[b.slots[j]]) return fail(ctx, SPDHG_ERR_STATE, "no template for a graph slot");

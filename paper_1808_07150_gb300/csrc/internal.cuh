@@ -135,7 +135,9 @@ struct TgvArgs {
   float* zu; float* zw;
   const float* Tu; float Tw;
   float sigma, alpha, inv_p;
+  float* bscr;                          // scratch: the dual change b (3N or 6N)
 };
+// the block's dual pass and primal pass (two kernels)
 cudaError_t launch_tgv(const DevGeom& g, const TgvArgs& a, cudaStream_t s);
 // data iteration for TGV also steps w: w -= Tw * zbar_w with zbar_w = zw (no new w-dual change)
 cudaError_t launch_w_step(const DevGeom& g, float* w, const float* zw, float Tw, cudaStream_t s);
@@ -199,6 +201,7 @@ struct spdhg_ctx {
   int wcur = 0;
   float* zw = nullptr;
   float* q2[2] = {nullptr, nullptr};
+  float* tgv_b = nullptr;      // TGV dual change of the current prior block (6N)
   int q2cur = 0;
   float Tw = 0.f;
   // scratch

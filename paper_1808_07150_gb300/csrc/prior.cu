@@ -225,13 +225,19 @@ cudaError_t launch_w_step(const DevGeom& g, float* w, const float* zw, float Tw,
   return cudaGetLastError();
 }
 
-// block 0: q+ = proj_{alpha0}(q + sigma (grad u - w)); dq = q+ - q; dzu = grad^T dq, dzw = -dq
-struct Tgv0 {
-  const DevGeom& g;
-  const TgvArgs& a;
-  int64_t N;
-  int sx, sy;
-  __device__ __forceinline__ void dual(int jx, int jy, int jz, int64_t j, float b[3], float qn[3]) const {
+// Each TGV block runs in two passes: the dual pass computes q+ = proj(q + sigma A x) and the dual
+// change b = q+ - q once per voxel (written to a scratch array), the primal pass forms A^T b from
+// b and its neighbours and takes the z, w and u steps.  The arithmetic per voxel, and the order
+// of every sum, is that of computing the neighbours' dual changes in place.
+
+// block 0: q+ = proj_{alpha0}(q + sigma (grad u - w)); b = q+ - q
+__global__ void __launch_bounds__(256) k_tgv0_dual(DevGeom g, TgvArgs a) {
+  const int64_t N = (int64_t)g.nx * g.ny * g.nz;
+  const int sx = g.nz, sy = g.nx * g.nz;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+    const int jz = (int)(j % g.nz);
+    const int64_t t = j / g.nz;
+    const int jx = (int)(t % g.nx), jy = (int)(t / g.nx);
     const float* u = a.u_in;
     const float c = u[j];
     float gr[3];
@@ -248,32 +254,32 @@ struct Tgv0 {
     const float sc = fmaxf(1.f, nrm / a.alpha);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      qn[k] = qa[k] / sc;
-      b[k] = qn[k] - qo[k];
+      const float qn = qa[k] / sc;
+      a.q_out[k * N + j] = qn;
+      a.bscr[k * N + j] = qn - qo[k];
     }
   }
-};
+}
 
-__global__ void __launch_bounds__(256) k_tgv0(DevGeom g, TgvArgs a) {
+// block 0: dzu = grad^T b, dzw = -b; z and primal steps of u and w
+__global__ void __launch_bounds__(256) k_tgv0_primal(DevGeom g, TgvArgs a) {
   const int64_t N = (int64_t)g.nx * g.ny * g.nz;
-  Tgv0 st{g, a, N, g.nz, g.nx * g.nz};
+  const int sx = g.nz, sy = g.nx * g.nz;
+  const float* bs = a.bscr;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N; idx += (int64_t)gridDim.x * blockDim.x) {
     const int iz = (int)(idx % g.nz);
     const int64_t t = idx / g.nz;
-    const int ix = (int)(t % g.nx);
-    const int iy = (int)(t / g.nx);
-    float b[3], qn[3], bm[3], tmp[3];
-    st.dual(ix, iy, iz, idx, b, qn);
+    const int ix = (int)(t % g.nx), iy = (int)(t / g.nx);
+    const float b[3] = {bs[idx], bs[N + idx], bs[2 * N + idx]};
     float dz = 0.f;
     if (ix < g.nx - 1) dz -= b[0];
     if (iy < g.ny - 1) dz -= b[1];
     if (iz < g.nz - 1) dz -= b[2];
-    if (ix > 0) { st.dual(ix - 1, iy, iz, idx - st.sx, bm, tmp); dz += bm[0]; }
-    if (iy > 0) { st.dual(ix, iy - 1, iz, idx - st.sy, bm, tmp); dz += bm[1]; }
-    if (iz > 0) { st.dual(ix, iy, iz - 1, idx - 1, bm, tmp); dz += bm[2]; }
+    if (ix > 0) dz += bs[idx - sx];
+    if (iy > 0) dz += bs[N + idx - sy];
+    if (iz > 0) dz += bs[2 * N + idx - 1];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      a.q_out[k * N + idx] = qn[k];
       // w part: dzw = -dq;  zw += dzw;  w = w - Tw (zw + dzw / p)
       const float dzw = -b[k];
       const float zwn = a.zw[k * N + idx] + dzw;
@@ -286,31 +292,35 @@ __global__ void __launch_bounds__(256) k_tgv0(DevGeom g, TgvArgs a) {
   }
 }
 
-// block 1: q+ = proj_{alpha1}(q + sigma E w); dq; dzw = E^T dq; u only takes its primal step.
-struct Tgv1 {
-  const DevGeom& g;
-  const TgvArgs& a;
-  int64_t N;
-  int sx, sy;
-  // backward difference of w component c along axis ax at voxel j (d-_a = -D_a^T)
-  __device__ __forceinline__ float dm(int c, int ax, int jx, int jy, int jz, int64_t j) const {
-    const float* wc = a.w_in + c * N;
-    const int ja = ax == 0 ? jx : (ax == 1 ? jy : jz);
-    const int na = ax == 0 ? g.nx : (ax == 1 ? g.ny : g.nz);
-    const int st = ax == 0 ? sx : (ax == 1 ? sy : 1);
-    float r = 0.f;
-    if (ja < na - 1) r += wc[j];
-    if (ja > 0) r -= wc[j - st];
-    return r;
-  }
-  __device__ __forceinline__ void dual(int jx, int jy, int jz, int64_t j, float b[6], float qn[6]) const {
+// backward difference of w component c along axis ax at voxel j (d-_a = -D_a^T)
+__device__ __forceinline__ float tgv_dm(const TgvArgs& a, const DevGeom& g, int64_t N, int c, int ax, int ja,
+                                        int na, int st, int64_t j) {
+  const float* wc = a.w_in + c * N;
+  float r = 0.f;
+  if (ja < na - 1) r += wc[j];
+  if (ja > 0) r -= wc[j - st];
+  return r;
+}
+
+// block 1: q+ = proj_{alpha1}(q + sigma E w) (Frobenius ball, off-diagonals counted twice)
+__global__ void __launch_bounds__(256) k_tgv1_dual(DevGeom g, TgvArgs a) {
+  const int64_t N = (int64_t)g.nx * g.ny * g.nz;
+  const int sx = g.nz, sy = g.nx * g.nz;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+    const int jz = (int)(j % g.nz);
+    const int64_t t = j / g.nz;
+    const int jx = (int)(t % g.nx), jy = (int)(t / g.nx);
+    auto dm = [&](int c, int ax) {
+      return ax == 0 ? tgv_dm(a, g, N, c, 0, jx, g.nx, sx, j)
+                     : (ax == 1 ? tgv_dm(a, g, N, c, 1, jy, g.ny, sy, j) : tgv_dm(a, g, N, c, 2, jz, g.nz, 1, j));
+    };
     float e[6];
-    e[0] = dm(0, 0, jx, jy, jz, j);
-    e[1] = dm(1, 1, jx, jy, jz, j);
-    e[2] = dm(2, 2, jx, jy, jz, j);
-    e[3] = 0.5f * (dm(1, 0, jx, jy, jz, j) + dm(0, 1, jx, jy, jz, j));
-    e[4] = 0.5f * (dm(2, 0, jx, jy, jz, j) + dm(0, 2, jx, jy, jz, j));
-    e[5] = 0.5f * (dm(2, 1, jx, jy, jz, j) + dm(1, 2, jx, jy, jz, j));
+    e[0] = dm(0, 0);
+    e[1] = dm(1, 1);
+    e[2] = dm(2, 2);
+    e[3] = 0.5f * (dm(1, 0) + dm(0, 1));
+    e[4] = 0.5f * (dm(2, 0) + dm(0, 2));
+    e[5] = 0.5f * (dm(2, 1) + dm(1, 2));
     float qo[6], qa[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
@@ -322,35 +332,30 @@ struct Tgv1 {
     const float sc = fmaxf(1.f, sqrtf(n2) / a.alpha);
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      qn[k] = qa[k] / sc;
-      b[k] = qn[k] - qo[k];
+      const float qn = qa[k] / sc;
+      a.q_out[k * N + j] = qn;
+      a.bscr[k * N + j] = qn - qo[k];
     }
   }
-};
+}
 
-__global__ void __launch_bounds__(256) k_tgv1(DevGeom g, TgvArgs a) {
+// block 1: dzw = E^T b; z and primal step of w; u takes its primal step with zbar_u = z_u
+__global__ void __launch_bounds__(256) k_tgv1_primal(DevGeom g, TgvArgs a) {
   const int64_t N = (int64_t)g.nx * g.ny * g.nz;
-  Tgv1 st{g, a, N, g.nz, g.nx * g.nz};
+  const int sx = g.nz, sy = g.nx * g.nz;
+  const float* bs = a.bscr;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < N; idx += (int64_t)gridDim.x * blockDim.x) {
     const int iz = (int)(idx % g.nz);
     const int64_t t = idx / g.nz;
-    const int ix = (int)(t % g.nx);
-    const int iy = (int)(t / g.nx);
-    float b[6], qn[6], bp[6], tmp[6];
-    st.dual(ix, iy, iz, idx, b, qn);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) a.q_out[k * N + idx] = qn[k];
+    const int ix = (int)(t % g.nx), iy = (int)(t / g.nx);
+    const bool hx = ix < g.nx - 1, hy = iy < g.ny - 1, hz = iz < g.nz - 1;
     // (d-_a)^T = -D_a:  ((d-_a)^T p)(k) = p(k) - p(k + e_a) for k_a < n_a - 1, else 0.
     // E^T dq:  w_c += sum over entries (a,b) of E containing d-_a w_c, weights 1 (diag) or 1
     // (off-diagonal: 2 in the inner product times the 1/2 of the definition).
-    float up[3][6];  // dq at k + e_a for a = x, y, z
-    const bool hx = ix < g.nx - 1, hy = iy < g.ny - 1, hz = iz < g.nz - 1;
-    if (hx) st.dual(ix + 1, iy, iz, idx + st.sx, up[0], tmp);
-    if (hy) st.dual(ix, iy + 1, iz, idx + st.sy, up[1], tmp);
-    if (hz) st.dual(ix, iy, iz + 1, idx + 1, up[2], tmp);
     auto dmT = [&](int comp, int ax) -> float {
       const bool h = ax == 0 ? hx : (ax == 1 ? hy : hz);
-      return h ? b[comp] - up[ax][comp] : 0.f;
+      const int st = ax == 0 ? sx : (ax == 1 ? sy : 1);
+      return h ? bs[comp * N + idx] - bs[comp * N + idx + st] : 0.f;
     };
     float dzw[3];
     dzw[0] = dmT(0, 0) + dmT(3, 1) + dmT(4, 2);
@@ -362,7 +367,6 @@ __global__ void __launch_bounds__(256) k_tgv1(DevGeom g, TgvArgs a) {
       a.zw[k * N + idx] = zwn;
       a.w_out[k * N + idx] = a.w_in[k * N + idx] - a.Tw * fmaf(dzw[k], a.inv_p, zwn);
     }
-    // u: no change of z_u in this block; zbar_u = z_u
     a.u_out[idx] = fmaxf(a.u_in[idx] - a.Tu[idx] * a.zu[idx], 0.f);
   }
 }
@@ -371,8 +375,14 @@ cudaError_t launch_tgv(const DevGeom& g, const TgvArgs& a, cudaStream_t s) {
   const int64_t N = (int64_t)g.nx * g.ny * g.nz;
   int64_t blocks = (N + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
-  if (a.block == 0) k_tgv0<<<(int)blocks, 256, 0, s>>>(g, a);
-  else k_tgv1<<<(int)blocks, 256, 0, s>>>(g, a);
+  if (!a.bscr) return cudaErrorInvalidValue;
+  if (a.block == 0) {
+    k_tgv0_dual<<<(int)blocks, 256, 0, s>>>(g, a);
+    k_tgv0_primal<<<(int)blocks, 256, 0, s>>>(g, a);
+  } else {
+    k_tgv1_dual<<<(int)blocks, 256, 0, s>>>(g, a);
+    k_tgv1_primal<<<(int)blocks, 256, 0, s>>>(g, a);
+  }
   return cudaGetLastError();
 }
 
