@@ -252,14 +252,15 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
   const int v = subset_view(g, subset, l);
   const Line L = make_line(g, v, r);
 
-  // planes of this thread: lane of warp-sized runs of one segment (run = warp + k * nwarps)
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // planes of this thread: lane of warp-sized runs of one segment (run = PPT * warp + k, so the
+  // runs of a warp are neighbours in the run table and usually share their segment)
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   int pseg[PPT], pq[PPT], pp[PPT];
   bool pvalid[PPT];
   float acc[PPT], chord[PPT];
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
-    const int run = wi + k * nwarps;
+    const int run = wi * PPT + k;
     acc[k] = 0.f;
     chord[k] = 0.f;
     pseg[k] = -1;
@@ -338,8 +339,53 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
     const float* xb = xs + buf * kFwdChunk * xs_stride;
     const float4* tl = tapL + buf * g.n_seg * kFwdChunk;
     const int4* tm = tapM + buf * g.n_seg * kFwdChunk;
+    // all runs of this warp in one segment (warp-uniform): one load of each entry's taps serves them
+    bool same = pseg[0] >= 0;
+#pragma unroll
+    for (int k = 1; k < PPT; ++k) same = same && (pseg[k] < 0 || pseg[k] == pseg[0]);
+    if (MODE != FWD_SIGMA && PPT > 1 && same) {
+      const float4* tlk = tl + pseg[0] * kFwdChunk;
+      const int4* tmk = tm + pseg[0] * kFwdChunk;
+      float sum[PPT];
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) sum[k] = 0.f;
+      for (int e = 0; e < ne; ++e) {
+        const int4 M = tmk[e];
+        const float4 Lv = tlk[e];
+        const float* xe = xb + M.x;
+        if (NT == 1 || M.z == 1) {  // tap count is uniform across the warp
+#pragma unroll
+          for (int k = 0; k < PPT; ++k)
+            if (pseg[k] >= 0 && (unsigned)(pq[k] - M.y) < (unsigned)(nz + PAD)) sum[k] = fmaf(Lv.x, xe[pq[k]], sum[k]);
+        } else if (NT == 2 || M.z == 2) {
+#pragma unroll
+          for (int k = 0; k < PPT; ++k)
+            if (pseg[k] >= 0 && (unsigned)(pq[k] - M.y) < (unsigned)(nz + PAD)) {
+              const float* xp = xe + pq[k];
+              sum[k] = fmaf(Lv.y, xp[-1], fmaf(Lv.x, xp[0], sum[k]));
+            }
+        } else if (NT == 3 || M.z == 3) {
+#pragma unroll
+          for (int k = 0; k < PPT; ++k)
+            if (pseg[k] >= 0 && (unsigned)(pq[k] - M.y) < (unsigned)(nz + PAD)) {
+              const float* xp = xe + pq[k];
+              sum[k] = fmaf(Lv.z, xp[-2], fmaf(Lv.y, xp[-1], fmaf(Lv.x, xp[0], sum[k])));
+            }
+        } else {
+#pragma unroll
+          for (int k = 0; k < PPT; ++k)
+            if (pseg[k] >= 0 && (unsigned)(pq[k] - M.y) < (unsigned)(nz + PAD)) {
+              const float* xp = xe + pq[k];
+              sum[k] = fmaf(Lv.w, xp[-3], fmaf(Lv.z, xp[-2], fmaf(Lv.y, xp[-1], fmaf(Lv.x, xp[0], sum[k]))));
+            }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) acc[k] += sum[k];
+    }
 #pragma unroll
     for (int k = 0; k < PPT; ++k) {
+      if (MODE != FWD_SIGMA && PPT > 1 && same) break;  // done above
       if (pseg[k] < 0) break;  // warp-uniform: no more runs for this warp
       const float4* tlk = tl + pseg[k] * kFwdChunk;
       const int4* tmk = tm + pseg[k] * kFwdChunk;
