@@ -67,6 +67,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value, device=None):
+    """The largest `value` over all ranks of the default process group (the value itself when
+    there is no group); the timing rule of the weak-scaling replicas."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, ws, seconds):
+    """Whole-job throughput of ws replicas that each processed units_per_rank units, timed by
+    the slowest rank."""
+    return ws * units_per_rank / seconds
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -296,13 +314,9 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     prof = ctx.spdhg_profile_read()
     ctx.spdhg_profile(False)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     ms_per_epoch = ms / args.steps
-    value = ws * args.steps / (ms / 1e3)
+    value = aggregate_rate(args.steps, ws, ms / 1e3)
 
     # roofline of the dominant kernel (per-launch CUDA events on the launching stream)
     dom = max(("forward", "backward", "prior"), key=lambda k: prof[k][0])
@@ -328,11 +342,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     barrier()
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dev)
     ctx2.close()
     h2d = (3 * M + 2 * N) * 4 / args.steps
     d2h = N * 4 / args.steps
@@ -356,7 +366,7 @@ def run_ours(args):
             "epoch_algorithmic_gbs": epoch_bytes / (ms_per_epoch / 1e3) / 1e9,
             "kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items() if v[1]},
             "gpu_launches": launches,
-            "e2e": {"value": ws * args.steps / e2e_s, "unit": "epoch/s", "h2d_bytes_per_step": int(h2d),
+            "e2e": {"value": aggregate_rate(args.steps, ws, e2e_s), "unit": "epoch/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h),
                     "what": "spdhg_set_data + spdhg_run(steps epochs) from pinned host buffers, x read back"},
             "clocks": clk,
