@@ -304,9 +304,12 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
     const int buf = c & 1;
     const int e0 = c * kFwdChunk, ne = min(kFwdChunk, n_ent - e0);
     float* xb = xs + buf * kFwdChunk * xs_stride;
-    for (int i = threadIdx.x; i < ne * nz; i += blockDim.x) {
-      const int e = i / nz, iz = i - e * nz;
-      cp_async4(xb + e * xs_stride + PAD + iz, a.x + ent[e0 + e].col * nz + iz);
+    // one warp per entry, lanes along z: no division or entry lookup per staged value
+    const int nw = blockDim.x >> 5;
+    for (int e = wi; e < ne; e += nw) {
+      const float* src = a.x + (size_t)ent[e0 + e].col * nz;
+      float* dst = xb + e * xs_stride + PAD;
+      for (int iz = lane; iz < nz; iz += 32) cp_async4(dst + iz, src + iz);
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     float4* tl = tapL + buf * g.n_seg * kFwdChunk;
