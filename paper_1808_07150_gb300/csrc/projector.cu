@@ -277,9 +277,11 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
     }
   }
   // zero pads of the staged columns (never overwritten by the copies)
-  for (int i = threadIdx.x; i < 2 * kFwdChunk * 2 * PAD; i += blockDim.x) {
-    const int col = i / (2 * PAD), k = i - col * (2 * PAD);
-    xs[col * xs_stride + (k < PAD ? k : nz + k)] = 0.f;
+  if constexpr (PAD > 0) {
+    for (int i = threadIdx.x; i < 2 * kFwdChunk * 2 * PAD; i += blockDim.x) {
+      const int col = i / (2 * PAD), k = i - col * (2 * PAD);
+      xs[col * xs_stride + (k < PAD ? k : nz + k)] = 0.f;
+    }
   }
   const bool ydom = fabsf(L.c_hi) >= fabsf(L.s_hi);  // |dy| >= |dx|: walk the rows of y
   const int nrows_all = ydom ? g.ny : g.nx;
@@ -531,12 +533,14 @@ __global__ void __launch_bounds__(kBwdWarps * 32, 3) k_backward(DevGeom g, int s
   for (int k = 0; k < ZK; ++k) acc[k] = 0.f;
   // padded position of every plane, and the zero frames of the staged rows (written once)
   for (int p = threadIdx.x; p < g.P; p += blockDim.x) seg_of[p] = p + (2 * g.plane_seg[p] + 1) * PAD;
-  for (int i = threadIdx.x; i < nr_tile * g.n_seg * 2 * PAD; i += blockDim.x) {
-    const int rr = i / (g.n_seg * 2 * PAD), rem = i - rr * (g.n_seg * 2 * PAD);
-    const int gi = rem / (2 * PAD), k = rem - gi * (2 * PAD);
-    const SegDev sd = g.seg[gi];
-    const int start = sd.p0 + 2 * gi * PAD;  // first slot of the segment's frame
-    sw[rr * p_pad + (k < PAD ? start + k : start + PAD + sd.n + (k - PAD))] = 0.f;
+  if constexpr (PAD > 0) {
+    for (int i = threadIdx.x; i < nr_tile * g.n_seg * 2 * PAD; i += blockDim.x) {
+      const int rr = i / (g.n_seg * 2 * PAD), rem = i - rr * (g.n_seg * 2 * PAD);
+      const int gi = rem / (2 * PAD), k = rem - gi * (2 * PAD);
+      const SegDev sd = g.seg[gi];
+      const int start = sd.p0 + 2 * gi * PAD;  // first slot of the segment's frame
+      sw[rr * p_pad + (k < PAD ? start + k : start + PAD + sd.n + (k - PAD))] = 0.f;
+    }
   }
   __syncthreads();
 
