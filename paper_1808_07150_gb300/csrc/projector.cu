@@ -505,7 +505,7 @@ constexpr int kBwdMaxItems = 64;         // (pair, segment) items per column and
 // compute the axial taps of every (pair, segment) item, and then gather along contiguous plane
 // runs from shared memory, lane = iz mod 32, ZK voxels per lane.
 template <int NT, int ZK, int MODE>
-__global__ void __launch_bounds__(kBwdWarps * 32, 3) k_backward(DevGeom g, int subset, int nr_tile, int p_pad,
+__global__ void __launch_bounds__(kBwdWarps * 32, 4) k_backward(DevGeom g, int subset, int nr_tile, int p_pad,
                                                              int bcap, BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int PAD = NT - 1;
@@ -763,8 +763,10 @@ cudaError_t launch_forward(const DevGeom& g, int subset, int mode, const FwdArgs
 }
 
 static int bwd_rows_per_tile(const DevGeom& g) {
-  // radial rows a tile's footprints can touch: spread of the tile centres plus one footprint
-  return (int)floorf((2.f * (kBwdTile - 1) + 1.4143f) * g.inv_drp) + 4;
+  // radial rows a tile's footprints can touch: the projection of the tile's pixel centres spans
+  // (kBwdTile - 1)(|c| + |s|) pixels and a footprint |c| + |s| more, at most kBwdTile sqrt(2);
+  // the kernel's rounding (ceil - 1 .. floor + 1) adds three rows, one more is margin
+  return (int)floorf(kBwdTile * 1.4143f * g.inv_drp) + 4;
 }
 
 template <int NT, int ZK, int MODE>
