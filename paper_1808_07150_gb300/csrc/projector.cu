@@ -503,9 +503,10 @@ constexpr int kBwdMaxItems = 64;         // (pair, segment) items per column and
 // run framed by NT-1 zeros so that taps leaving the segment read zeros.  Each warp owns one
 // column: its lanes find the footprint (bin, pixel interval) pairs, compact them with a ballot,
 // compute the axial taps of every (pair, segment) item, and then gather along contiguous plane
-// runs from shared memory, lane = iz mod 32, ZK voxels per lane.
+// runs from shared memory, lane = iz mod 32, ZK voxels per lane.  Up to 128 slices (ZK <= 4) four
+// blocks share an SM (32 registers per thread); with eight accumulators per lane, three.
 template <int NT, int ZK, int MODE>
-__global__ void __launch_bounds__(kBwdWarps * 32, 4) k_backward(DevGeom g, int subset, int nr_tile, int p_pad,
+__global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(DevGeom g, int subset, int nr_tile, int p_pad,
                                                              int bcap, BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int PAD = NT - 1;
