@@ -16,10 +16,18 @@ import numpy as np
 from . import _native
 
 # ----------------------------------------------------------------------------------------
-# projection operator P = diag(mult) L  (Sec. 1.2: "P performs the projection and includes
-# geometric factors, attenuation and normalization"); A_i = P_i for the data blocks (Eq.
-# EQU:SETTING:TV).  Subset i = views v with v mod m == i ("equidistantly divided angles", Sec. 4).
+# projection operator P = diag(mult) L  (Sec. 1.2: the projection model carries the geometric,
+# attenuation and normalisation factors, here the per-bin multiplier); A_i = P_i for the data
+# blocks (Eq. EQU:SETTING:TV).  Subset i = views v with v mod m == i (Sec. 4: subsets are formed
+# from evenly spaced view angles).
 # ----------------------------------------------------------------------------------------
+
+
+def bin_subsets(sc):
+    """True when the subsets interleave single bins (bin j of the flattened sinogram belongs to
+    subset j mod m: the paper's stability example of Sec. 1.3 divides the bins equidistantly),
+    False for view-interleaved subsets."""
+    return getattr(sc, "subset_kind", "views") == "bins"
 
 
 def subset_mask(sc, i):
@@ -27,6 +35,8 @@ def subset_mask(sc, i):
     m = np.zeros(sc.sino_shape, bool)
     if i < 0:
         m[:] = True
+    elif bin_subsets(sc):
+        m.ravel()[i::sc.n_subsets] = True
     else:
         m[i::sc.n_subsets] = True
     return m
@@ -34,7 +44,10 @@ def subset_mask(sc, i):
 
 def project(sc, x, subset=-1, mult=None):
     """P_i x (float64, full sinogram shape; bins outside subset i are 0)."""
-    y = _native.line_integrals(sc, x, subset)
+    if subset >= 0 and bin_subsets(sc):
+        y = _native.line_integrals(sc, x, -1) * subset_mask(sc, subset)
+    else:
+        y = _native.line_integrals(sc, x, subset)
     if mult is not None:
         y *= mult
     return y
@@ -45,6 +58,8 @@ def backproject(sc, y, subset=-1, mult=None):
     y = np.asarray(y, np.float64)
     if mult is not None:
         y = y * mult
+    if subset >= 0 and bin_subsets(sc):
+        return _native.line_integrals_adjoint(sc, y * subset_mask(sc, subset), -1)
     return _native.line_integrals_adjoint(sc, y, subset)
 
 
@@ -285,9 +300,17 @@ def splitmix64(seed, k):
     return z ^ (z >> 31)
 
 
-def probabilities(m, prior, sampling="balanced"):
+def probabilities(m, prior, sampling="balanced", custom=None):
+    """p_i of the m data blocks followed by the prior blocks.  sampling = "custom" takes the
+    given positive p (Remark "Sampling": any independent draws with p_i > 0 keep the convergence
+    of Theorem "Convergence"; the Discussion leaves choosing them to future work)."""
     nb = prior.n_blocks if prior is not None else 0
     n = m + nb
+    if sampling == "custom":
+        p = np.asarray(custom, np.float64)
+        if p.shape != (n,) or np.any(p <= 0) or abs(p.sum() - 1.0) > 1e-12:
+            raise ValueError("custom probabilities: n positive values summing to one")
+        return p.copy()
     if nb == 0 or sampling == "uniform":
         return np.full(n, 1.0 / n)
     p = np.empty(n)
@@ -594,6 +617,25 @@ def mlem(prob, n_iter, x0=None):
         ratio = prob.b / (project(sc, u, -1, prob.mult) + prob.r)
         with np.errstate(divide="ignore", invalid="ignore"):
             u = np.where(sens > 0, u / sens * backproject(sc, ratio, -1, prob.mult), 0.0)
+    return u
+
+
+def osem(prob, n_epochs, x0=None, order=None):
+    """OSEM (Eq. EQU:OSEM): sub-iteration k uses subset i = order[k mod m] (default i = k mod m)
+    and sets u <- u / (P_i^T 1) * P_i^T (b_i / (P_i u + r_i)); u = 0 where P_i^T 1 = 0.  One epoch
+    is m sub-iterations."""
+    sc = prob.sc
+    m = sc.n_subsets
+    order = list(range(m)) if order is None else [int(i) for i in order]
+    sens = [backproject(sc, np.ones(sc.sino_shape), i, prob.mult) for i in range(m)]
+    u = np.ones(sc.image_shape) if x0 is None else np.array(x0, np.float64)
+    for _ in range(n_epochs):
+        for k in range(m):
+            i = order[k % len(order)]
+            mask = subset_mask(sc, i)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                ratio = np.where(mask, prob.b / (project(sc, u, i, prob.mult) + prob.r), 0.0)
+                u = np.where(sens[i] > 0, u / sens[i] * backproject(sc, ratio, i, prob.mult), 0.0)
     return u
 
 

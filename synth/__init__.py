@@ -54,6 +54,7 @@ class Scanner:
     seg_dz: tuple
     n_subsets: int
     name: str = ""
+    subset_kind: str = "views"  # "views": view-interleaved subsets; "bins": bin j in subset j mod m
 
     @property
     def n_planes(self) -> int:
@@ -75,8 +76,8 @@ class Scanner:
     def sino_shape(self):
         return (self.n_views, self.n_radial, self.n_planes)
 
-    def with_subsets(self, m: int) -> "Scanner":
-        return dataclasses.replace(self, n_subsets=m)
+    def with_subsets(self, m: int, kind: str = None) -> "Scanner":
+        return dataclasses.replace(self, n_subsets=m, subset_kind=self.subset_kind if kind is None else kind)
 
     def plane_table(self):
         """Per-plane (z_mid, dz) in plane order (segment-major)."""
@@ -92,7 +93,7 @@ class Scanner:
 
 
 def subset_views(g: Scanner, i: int):
-    """Views of the view-interleaved subset i ("equidistantly divided angles")."""
+    """Views of the view-interleaved subset i (evenly spaced view angles)."""
     return list(range(i, g.n_views, g.n_subsets))
 
 
