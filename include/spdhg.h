@@ -18,11 +18,11 @@
  *   LOR       P(t) = (s cos - t sin, s sin + t cos, z_mid + t dz/(2h)), t in [-h, h],
  *             h = sqrt(radius^2 - s^2): the chord between two points of the detector cylinder.
  *   projector (L x)_j = sum_k |LOR_j intersect voxel_k| x_k, lengths in units of vx; a line lying
- *             in a grid plane belongs to the voxel whose lower face holds it.  P = diag(mult) L
- *             ("P performs the projection and includes geometric factors, attenuation and
- *             normalization", Sec. 1.2).
- *   subsets   view-interleaved: subset i = views v with v mod n_subsets == i ("subsets with
- *             equidistantly divided angles", Sec. 4).
+ *             in a grid plane belongs to the voxel whose lower face holds it.  P = diag(mult) L:
+ *             the per-bin multiplier carries the geometric, attenuation and normalisation
+ *             factors of the projection model (Sec. 1.2).
+ *   subsets   view-interleaved: subset i = views v with v mod n_subsets == i (Sec. 4 forms the
+ *             subsets from evenly spaced view angles), or bin-interleaved (subset_kind).
  *   blocks    SPDHG block indices 0..m-1 are the data subsets; m (and m+1 for TGV) the prior.
  *
  * Errors: every call returns SPDHG_OK (0) or a negative spdhg_status; no call aborts the process.
@@ -71,12 +71,19 @@ typedef struct {
   const double* seg_zmid0;    /* LOR mid-point z of the segment's first plane, mm */
   const double* seg_dzmid;    /* plane spacing within the segment; must equal vz if seg_n > 1 */
   const double* seg_dz;       /* axial separation z2 - z1 of the segment's LOR ends, mm */
-  int n_subsets;              /* m, number of view-interleaved data subsets */
+  int n_subsets;              /* m, number of data subsets */
+  int subset_kind;            /* SPDHG_SUBSETS_VIEWS (0): subset i = views v with v mod m == i;
+                                 SPDHG_SUBSETS_BINS (1): subset i = bins j of the flattened sinogram
+                                 with j mod m == i (the equidistantly divided bins of the stability
+                                 example of Sec. 1.3).  A bin subset touches every view, so its
+                                 projection costs a full projection */
 } spdhg_geometry;
+
+enum { SPDHG_SUBSETS_VIEWS = 0, SPDHG_SUBSETS_BINS = 1 };
 
 enum { SPDHG_PRIOR_NONE = 0, SPDHG_PRIOR_TV = 1, SPDHG_PRIOR_DTV = 2, SPDHG_PRIOR_ATV = 3,
        SPDHG_PRIOR_TGV = 4 };
-enum { SPDHG_SAMPLING_BALANCED = 0, SPDHG_SAMPLING_UNIFORM = 1 };
+enum { SPDHG_SAMPLING_BALANCED = 0, SPDHG_SAMPLING_UNIFORM = 1, SPDHG_SAMPLING_CUSTOM = 2 };
 
 typedef struct {
   int prior;                  /* SPDHG_PRIOR_* */
@@ -84,7 +91,8 @@ typedef struct {
   double alpha0, alpha1;      /* TGV: alpha0 ||grad u - w|| + alpha1 ||E w|| (Sec. 4.3) */
   double dtv_gamma;           /* dTV: D = I - dtv_gamma xi xi^T, 0 <= dtv_gamma < 1 */
   double dtv_eta_frac;        /* dTV: xi = grad v / sqrt(|grad v|^2 + eta^2), eta = frac*max|grad v| */
-  int sampling;               /* SPDHG_SAMPLING_*: balanced = prior w.p. 1/2 (Sec. 4.2) */
+  int sampling;               /* SPDHG_SAMPLING_*: balanced = prior w.p. 1/2 (Sec. 4.2); custom =
+                                 the probabilities in `probs` */
   int precond;                /* 1: Eq. EQU:STEPSIZE:PRECOND for data blocks; 0: scalar Eq.
                                  EQU:STEPSIZE:SCALAR with ||P_i|| by power iteration on P_i^T P_i
                                  from the constant vector, until the eigenvalue changes by less than
@@ -96,6 +104,20 @@ typedef struct {
   int objective_every;        /* spdhg_run: evaluate Psi every k epochs (0: never) */
   int graph;                  /* spdhg_run: 1 = every epoch is one CUDA graph launch (the path of
                                  spdhg_run_batch); 0 = kernels launched one by one */
+  double target_gap;          /* spdhg_run / spdhg_run_batch: > 0 stops the run at the first
+                                 evaluated epoch whose relative objective
+                                 (Psi(x^k) - psi_star) / (Psi(0) - psi_star) is <= target_gap (the
+                                 measure of Sec. 4, normalised by the zero image for every start);
+                                 the objective is then evaluated every objective_every epochs, or
+                                 every epoch if objective_every is 0.  0: run all epochs */
+  double psi_star;            /* Psi(x*) of an approximate minimiser, used by target_gap */
+  const float* x_star;        /* NULL, or an approximate minimiser x* (N floats, device memory):
+                                 the report then receives PSNR(x^k, x*) (Sec. 4) at every evaluated
+                                 epoch */
+  const double* probs;        /* SPDHG_SAMPLING_CUSTOM: p_i of the n blocks (data subsets, then
+                                 the prior blocks), each > 0, summing to 1 (Remark "Sampling": any
+                                 proper sampling converges; the step sizes T_i use these p_i).
+                                 Read by spdhg_setup only */
 } spdhg_params;
 
 typedef struct {
@@ -104,6 +126,15 @@ typedef struct {
   double* objective;          /* caller array of epochs+1 doubles or NULL: Psi after each
                                  evaluated epoch (index 0 = start), NaN where not evaluated */
   double* epoch_ms;           /* caller array of `epochs` doubles or NULL: device time per epoch */
+  double* psnr;               /* caller array of epochs+1 doubles or NULL: PSNR(x^k, x*) =
+                                 20 log10(max|x*| / ||x^k - x*||_2) after each evaluated epoch
+                                 (index 0 = start; needs params.x_star), NaN where not evaluated */
+  int stop_epoch;             /* epochs after which the relative objective first reached
+                                 params.target_gap (-1: not reached, or no target) */
+  double ms_to_stop;          /* device time of the epochs up to stop_epoch (solver time only:
+                                 objective evaluations excluded); NaN if not reached */
+  double psi_zero;            /* Psi(0), the normaliser of the relative objective (NaN without a
+                                 target) */
 } spdhg_report;
 
 /* Creates a context for a geometry on the current CUDA device (device tables, no data yet).
@@ -181,6 +212,23 @@ int spdhg_load_state(spdhg_ctx* ctx, const char* path);
  * out[2] = out[0] + out[1].  x = NULL uses the context's current iterate (and w for TGV). */
 int spdhg_objective(spdhg_ctx* ctx, const float* x, int where, double out[3], void* stream);
 
+/* OSEM (Eq. EQU:OSEM) or, with mlem = 1, MLEM (Eq. EQU:MLEM) on the context's data: the
+ * unregularised expectation-maximisation baselines the paper compares SPDHG with (Sec. 1.3).  One
+ * epoch is m sub-iterations u <- u / (P_i^T 1) * P_i^T (b_i / (P_i u + r_i)), i = k mod m (one
+ * iteration over all bins for MLEM); u = 0 where P_i^T 1 = 0.  The start image comes from x_inout
+ * (host or device per `where`; NULL: ones) and the result is written back to it.  From `params`
+ * only epochs, objective_every, target_gap / psi_star and x_star are used (as in spdhg_run; the
+ * objective is the data term, no prior).  The sensitivity images P_i^T 1 are computed on the first
+ * call after spdhg_set_data and kept (m x N floats for OSEM, N for MLEM).  The call replaces the
+ * context's iterate: run spdhg_setup before further SPDHG iterations. */
+int spdhg_osem(spdhg_ctx* ctx, const spdhg_params* params, int mlem, float* x_inout, int where,
+               spdhg_report* report, void* stream);
+
+/* PSNR(x, x*) = 20 log10(max|x*| / ||x - x*||_2) (Sec. 4; log base 10) in FP64 on the GPU.  x and
+ * x_star are N floats in host or device memory per `where` (x = NULL: the context's current
+ * iterate). */
+int spdhg_psnr(spdhg_ctx* ctx, const float* x, const float* x_star, int where, double* out, void* stream);
+
 /* Sampling probabilities p_i of the blocks for the current parameters (Sec. 4.2). */
 int spdhg_probabilities(const spdhg_ctx* ctx, double* probs, int* n_blocks);
 
@@ -192,7 +240,10 @@ int spdhg_sample(uint64_t seed, uint64_t offset, int n, const double* probs, int
 
 /* Full reconstruction: spdhg_setup(params, x_inout) then params->epochs epochs of
  * iterations_per_epoch draws each (2m for balanced sampling), evaluating Psi every
- * objective_every epochs; the final iterate is written back to x_inout (host or device). */
+ * objective_every epochs (FP64 on the GPU); with params->target_gap > 0 the run stops after the
+ * first evaluated epoch whose relative objective reaches the target (Sec. 4) and the report
+ * gives that epoch and the solver time to it.  A non-finite objective ends the run with
+ * SPDHG_ERR_DIVERGED.  The final iterate is written back to x_inout (host or device). */
 int spdhg_run(spdhg_ctx* ctx, const spdhg_params* params, float* x_inout, int where,
               spdhg_report* report, void* stream);
 
@@ -201,9 +252,11 @@ int spdhg_run(spdhg_ctx* ctx, const spdhg_params* params, float* x_inout, int wh
  * a library call cudaMalloc (device memory owned by their own pool with a hard budget, or loops
  * where an allocation's device synchronisation is not acceptable).  Its scratch is a fixed
  * device array of 2^21 floats (8 MiB) inside the library, held by every device that loads the
- * library until the process exits; a subset with more bins is rejected with SPDHG_ERR_ARG.  The
- * first call on a device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls share the array and
+ * library until the process exits; a subset with more bins is rejected with SPDHG_ERR_ARG.  Every
+ * call looks up the array's device address (cudaGetSymbolAddress) with the context's device
+ * current, so a reset of the device's primary context does not leave a stale address behind; the
+ * first call on a device may also load the library's device code, so make that first call before
+ * any stream capture.  All calls share the array and
  * every call overwrites the part it reads, so nothing has to be cleared between calls, but calls
  * whose work overlaps on the GPU (concurrent streams, several contexts) race on it.  x and y are
  * device pointers as in spdhg_backproject. */
@@ -214,8 +267,11 @@ int spdhg_backproject_noalloc(spdhg_ctx* ctx, const float* y, float* x, int subs
 enum { SPDHG_TUNE_PRIOR_COLS = 0,   /* prior kernel: voxel columns per block, incl. one halo column
                                        (blocks of up to 32 warps) */
        SPDHG_TUNE_PRIOR_YCHUNK = 1, /* prior kernel: rows marched per block */
-       SPDHG_TUNE_FWD_SPLIT = 2,    /* forward kernel: blocks sharing the planes of one LOR line */
-       SPDHG_TUNE_FWD_WARPS = 3,    /* forward kernel: warps per block (4, 8 or 16) */
+       SPDHG_TUNE_FWD_SPLIT = 2,    /* forward kernel: row parts of one LOR line (partial sums
+                                       reduced in a fixed order) */
+       SPDHG_TUNE_FWD_WARPS = 3,    /* forward kernel: warps per block (1, 2, 4, 8 or 16); a warp
+                                       owns two runs of 32 planes, so a line's runs are spread
+                                       over ceil(runs / (2 * warps)) blocks */
        SPDHG_TUNE_PRIOR_STAGES = 4, /* prior kernel: rows in its shared-memory pipeline (3 or 4) */
        SPDHG_TUNE_KNOBS = 8 };
 

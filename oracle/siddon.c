@@ -3,7 +3,7 @@
  * and the bench's CPU-baseline leg use it; the CUDA library never links or calls it).
  *
  * The projection operator P of the PET problem (Sec. 1.2, Eq. EQU:PROB:OPT) is not specified
- * by the paper beyond "geometric factors, attenuation and normalization"; this file computes
+ * by the paper beyond its geometric, attenuation and normalisation factors; this file computes
  * its geometric part L as the exact line integral of the piecewise-constant image along each
  * line of response:  (L x)_j = sum_k len(LOR_j  intersect voxel_k) * x_k,  lengths in units of
  * the transaxial voxel size.  Per-bin multipliers are applied by the Python layer.

@@ -147,6 +147,15 @@ class Context:
         self._check(_capi.lib().spdhg_objective(self.h, px[0], px[1], out, _stream(stream)))
         return out[0], out[1], out[2]
 
+    def spdhg_psnr(self, x_star, x=None, stream=None):
+        """PSNR(x, x*) in dB (x = None: the current iterate)."""
+        ps = _capi.pointer(x_star, self.n_voxels)
+        px = _capi.pointer(x, self.n_voxels)
+        where = _same_where(ps, px)
+        out = ctypes.c_double()
+        self._check(_capi.lib().spdhg_psnr(self.h, px[0], ps[0], where, ctypes.byref(out), _stream(stream)))
+        return out.value
+
     def spdhg_probabilities(self):
         n = ctypes.c_int()
         self._check(_capi.lib().spdhg_probabilities(self.h, None, ctypes.byref(n)))
@@ -159,6 +168,15 @@ class Context:
         rep, keep = _report(params)
         self._check(_capi.lib().spdhg_run(self.h, ctypes.byref(params), px[0], px[1], ctypes.byref(rep),
                                           _stream(stream)))
+        return _report_dict(rep, keep, params)
+
+    def spdhg_osem(self, params, x=None, mlem=False, stream=None):
+        """OSEM (or MLEM with mlem=True) for params.epochs epochs from x (None: ones); x receives
+        the result.  Returns the report dict as spdhg_run does."""
+        px = _capi.pointer(x, self.n_voxels)
+        rep, keep = _report(params)
+        self._check(_capi.lib().spdhg_osem(self.h, ctypes.byref(params), int(bool(mlem)), px[0], px[1],
+                                           ctypes.byref(rep), _stream(stream)))
         return _report_dict(rep, keep, params)
 
     def spdhg_autotune(self, reps=10, stream=None):
@@ -188,15 +206,18 @@ class Context:
 def _report(params):
     obj = np.full(params.epochs + 1, np.nan)
     ms = np.zeros(max(params.epochs, 1))
-    rep = _capi.Report(0, 0, obj.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                       ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
-    return rep, (obj, ms)
+    psnr = np.full(params.epochs + 1, np.nan)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rep = _capi.Report(0, 0, obj.ctypes.data_as(dp), ms.ctypes.data_as(dp), psnr.ctypes.data_as(dp), -1, np.nan,
+                       np.nan)
+    return rep, (obj, ms, psnr)
 
 
 def _report_dict(rep, keep, params):
-    obj, ms = keep
+    obj, ms, psnr = keep
     return dict(epochs_done=rep.epochs_done, iterations_done=rep.iterations_done, objective=obj,
-                epoch_ms=ms[:params.epochs])
+                epoch_ms=ms[:params.epochs], psnr=psnr, stop_epoch=rep.stop_epoch, ms_to_stop=rep.ms_to_stop,
+                psi_zero=rep.psi_zero)
 
 
 def spdhg_run_batch(contexts, params, xs=None, stream=None):

@@ -17,7 +17,8 @@ OK = 0
 ERR_ARG, ERR_CUDA, ERR_OOM, ERR_DATA, ERR_TIMEOUT, ERR_DIVERGED, ERR_STATE, ERR_UNSUPPORTED = range(-1, -9, -1)
 WHERE_HOST, WHERE_DEVICE = 0, 1
 PRIOR = {"none": 0, "tv": 1, "dtv": 2, "atv": 3, "tgv": 4}
-SAMPLING = {"balanced": 0, "uniform": 1}
+SAMPLING = {"balanced": 0, "uniform": 1, "custom": 2}
+SUBSETS = {"views": 0, "bins": 1}
 STATE = {"x": 0, "z": 1, "T": 2, "y": 3, "q": 4, "sigma": 5, "w": 6, "zw": 7, "q2": 8}
 
 _EXPORTS = [
@@ -25,7 +26,7 @@ _EXPORTS = [
     "spdhg_project", "spdhg_backproject", "spdhg_setup", "spdhg_iterate", "spdhg_get",
     "spdhg_objective", "spdhg_probabilities", "spdhg_sample", "spdhg_run", "spdhg_profile",
     "spdhg_profile_read", "spdhg_backproject_noalloc", "spdhg_tune", "spdhg_autotune",
-    "spdhg_run_batch", "spdhg_set", "spdhg_save_state", "spdhg_load_state",
+    "spdhg_run_batch", "spdhg_set", "spdhg_save_state", "spdhg_load_state", "spdhg_psnr", "spdhg_osem",
     "unet_gemm", "unet_device_error", "unet_create", "unet_destroy", "unet_last_error", "unet_num_params",
     "unet_set_params", "unet_init", "unet_get_params", "unet_get_grads", "unet_forward", "unet_backward", "unet_adam_step",
 ]
@@ -48,7 +49,7 @@ class Geometry(ctypes.Structure):
         ("radius", ctypes.c_double), ("n_segments", ctypes.c_int),
         ("seg_n", ctypes.POINTER(ctypes.c_int)), ("seg_zmid0", ctypes.POINTER(ctypes.c_double)),
         ("seg_dzmid", ctypes.POINTER(ctypes.c_double)), ("seg_dz", ctypes.POINTER(ctypes.c_double)),
-        ("n_subsets", ctypes.c_int),
+        ("n_subsets", ctypes.c_int), ("subset_kind", ctypes.c_int),
     ]
 
 
@@ -59,6 +60,8 @@ class Params(ctypes.Structure):
         ("sampling", ctypes.c_int), ("precond", ctypes.c_int), ("rho", ctypes.c_double),
         ("gamma", ctypes.c_double), ("seed", ctypes.c_uint64), ("epochs", ctypes.c_int),
         ("objective_every", ctypes.c_int), ("graph", ctypes.c_int),
+        ("target_gap", ctypes.c_double), ("psi_star", ctypes.c_double), ("x_star", ctypes.c_void_p),
+        ("probs", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -66,6 +69,8 @@ class Report(ctypes.Structure):
     _fields_ = [
         ("epochs_done", ctypes.c_int), ("iterations_done", ctypes.c_int64),
         ("objective", ctypes.POINTER(ctypes.c_double)), ("epoch_ms", ctypes.POINTER(ctypes.c_double)),
+        ("psnr", ctypes.POINTER(ctypes.c_double)), ("stop_epoch", ctypes.c_int), ("ms_to_stop", ctypes.c_double),
+        ("psi_zero", ctypes.c_double),
     ]
 
 
@@ -110,6 +115,8 @@ def lib():
             "spdhg_tune": ([vp, i32, i32], i32),
             "spdhg_autotune": ([vp, i32, P(i32), vp], i32),
             "spdhg_run_batch": ([P(vp), P(Params), P(vp), i32, i32, P(Report), vp], i32),
+            "spdhg_psnr": ([vp, vp, vp, i32, P(dp), vp], i32),
+            "spdhg_osem": ([vp, P(Params), i32, vp, i32, P(Report), vp], i32),
             "unet_gemm": ([vp, vp, vp, i32, i32, i32, i32, vp], i32),
             "unet_device_error": ([vp], i32),
             "unet_create": ([i32, P(i32), i32, i32, i32, P(vp)], i32),
@@ -148,15 +155,28 @@ def make_geometry(sc):
     keep = [(ctypes.c_int * n)(*sc.seg_n), (ctypes.c_double * n)(*sc.seg_zmid0),
             (ctypes.c_double * n)(*sc.seg_dzmid), (ctypes.c_double * n)(*sc.seg_dz)]
     g = Geometry(sc.nx, sc.ny, sc.nz, sc.vx, sc.vy, sc.vz, sc.n_radial, sc.d_radial, sc.n_views,
-                 sc.radius, n, keep[0], keep[1], keep[2], keep[3], sc.n_subsets)
+                 sc.radius, n, keep[0], keep[1], keep[2], keep[3], sc.n_subsets,
+                 SUBSETS[getattr(sc, "subset_kind", "views")])
     return g, keep
 
 
 def make_params(prior="tv", alpha=0.1, alpha0=0.2, alpha1=0.1, dtv_gamma=0.995, dtv_eta_frac=0.01,
                 sampling="balanced", precond=True, rho=0.99, gamma=1.0, seed=1808, epochs=1,
-                objective_every=0, graph=False):
-    return Params(PRIOR[prior], alpha, alpha0, alpha1, dtv_gamma, dtv_eta_frac, SAMPLING[sampling],
-                  int(bool(precond)), rho, gamma, seed, epochs, objective_every, int(bool(graph)))
+                objective_every=0, graph=False, target_gap=0.0, psi_star=0.0, x_star=None, probs=None):
+    """spdhg_params; x_star (an approximate minimiser for the PSNR log) is a device tensor, kept
+    alive by the caller for as long as the parameters are used; probs (sampling="custom") are the
+    block probabilities, kept alive with the returned structure."""
+    xs = None if x_star is None else ctypes.c_void_p(x_star.data_ptr())
+    pp = None
+    if probs is not None:
+        arr = np.ascontiguousarray(probs, np.float64)
+        pp = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    p = Params(PRIOR[prior], alpha, alpha0, alpha1, dtv_gamma, dtv_eta_frac, SAMPLING[sampling],
+               int(bool(precond)), rho, gamma, seed, epochs, objective_every, int(bool(graph)),
+               float(target_gap), float(psi_star), xs, pp)
+    if probs is not None:
+        p._probs_keep = arr
+    return p
 
 
 def pointer(a, numel=None, dtype=np.float32):

@@ -40,9 +40,15 @@ __global__ void k_fill(float* p, int64_t n, float v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
 
+// per-bin value of the bin's subset (bin subsets: bin j belongs to subset j mod m)
+__global__ void k_fill_bins(float* p, int64_t n, int m, const float* per_subset) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = per_subset[i % m];
+}
+
 __global__ void k_clamp_copy(float* dst, const float* src, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = fmaxf(src[i], 0.f);
+    dst[i] = prox_nonneg(src[i]);
 }
 
 // T = min(T, t_prior); voxels that no block sees (+inf) get T = 0.
@@ -160,26 +166,26 @@ int prepare_forward(spdhg_ctx* ctx, int subset, FwdArgs& a, cudaStream_t s) {
   const int split = forward_split(ctx->dg, subset);
   if (split <= 1) return SPDHG_OK;
   const size_t lines = (size_t)subset_views(ctx->dg, subset) * ctx->dg.R;
+  const size_t tickets = lines * forward_parts(ctx->dg);
   const size_t need = lines * split * ctx->dg.P;
   if (need > ctx->fwd_part_cap) {
     ++ctx->graph_gen;  // captured iterations hold the old address
     if (ctx->fwd_part) cudaFree(ctx->fwd_part);
     ctx->fwd_part = nullptr;
     ctx->fwd_part_cap = 0;
-    CK(cudaMalloc(&ctx->fwd_part, 2 * need * sizeof(float)));
+    CK(cudaMalloc(&ctx->fwd_part, need * sizeof(float)));
     ctx->fwd_part_cap = need;
   }
-  if (lines > ctx->fwd_ticket_cap) {
+  if (tickets > ctx->fwd_ticket_cap) {
     ++ctx->graph_gen;
     if (ctx->fwd_tickets) cudaFree(ctx->fwd_tickets);
     ctx->fwd_tickets = nullptr;
     ctx->fwd_ticket_cap = 0;
-    CK(cudaMalloc(&ctx->fwd_tickets, lines * sizeof(unsigned)));
-    CK(cudaMemsetAsync(ctx->fwd_tickets, 0, lines * sizeof(unsigned), s));
-    ctx->fwd_ticket_cap = lines;
+    CK(cudaMalloc(&ctx->fwd_tickets, tickets * sizeof(unsigned)));
+    CK(cudaMemsetAsync(ctx->fwd_tickets, 0, tickets * sizeof(unsigned), s));
+    ctx->fwd_ticket_cap = tickets;
   }
   a.part_acc = ctx->fwd_part;
-  a.part_chord = ctx->fwd_part + ctx->fwd_part_cap;
   a.tickets = ctx->fwd_tickets;
   a.part_cap = ctx->fwd_part_cap;
   a.ticket_cap = ctx->fwd_ticket_cap;
@@ -368,8 +374,9 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   if (!geom || !geom->seg_n || !geom->seg_zmid0 || !geom->seg_dzmid || !geom->seg_dz) return SPDHG_ERR_ARG;
   const spdhg_geometry& g = *geom;
   if (g.nx < 1 || g.ny < 1 || g.nz < 1 || g.n_radial < 1 || g.n_views < 1 || g.n_segments < 1 ||
-      g.n_subsets < 1 || g.n_subsets > g.n_views || !(g.vx > 0) || !(g.vy > 0) || !(g.vz > 0) ||
-      !(g.d_radial > 0) || !(g.radius > 0))
+      g.n_subsets < 1 || !(g.vx > 0) || !(g.vy > 0) || !(g.vz > 0) || !(g.d_radial > 0) || !(g.radius > 0) ||
+      (g.subset_kind != SPDHG_SUBSETS_VIEWS && g.subset_kind != SPDHG_SUBSETS_BINS) ||
+      (g.subset_kind == SPDHG_SUBSETS_VIEWS && g.n_subsets > g.n_views))
     return SPDHG_ERR_ARG;
   if (fabs(g.vx - g.vy) > 1e-9 * g.vx) return SPDHG_ERR_UNSUPPORTED;
   if (g.n_segments > kMaxSeg || g.nz > 256) return SPDHG_ERR_UNSUPPORTED;
@@ -384,12 +391,7 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
     P += g.seg_n[k];
     kappa_max = std::max(kappa_max, fabs(g.seg_dz[k]) / (2.0 * hmin * g.vz));
   }
-  if (P > 512 * kMaxPlanesPerThread) return SPDHG_ERR_UNSUPPORTED;
-  {
-    int n_runs = 0;
-    for (int k = 0; k < g.n_segments; ++k) n_runs += (g.seg_n[k] + 31) / 32;
-    if (n_runs > 64) return SPDHG_ERR_UNSUPPORTED;  // the forward kernel holds <= 4 runs per warp, 16 warps
-  }
+  if (P > 8192) return SPDHG_ERR_UNSUPPORTED;
   // kernels index images (up to 6 components) and sinograms with 32-bit integers
   if ((double)g.nx * g.ny * g.nz * 6 >= 2147483647.0 || (double)g.n_views * g.n_radial * P >= 2147483647.0)
     return SPDHG_ERR_UNSUPPORTED;
@@ -412,7 +414,14 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   cudaGetDevice(&ctx->device);
   ctx->N = (int64_t)g.nx * g.ny * g.nz;
   ctx->M = (int64_t)g.n_views * g.n_radial * P;
-  ctx->max_subset_bins = (int64_t)((g.n_views + g.n_subsets - 1) / g.n_subsets) * g.n_radial * P;
+  // a view subset's local sinogram holds its views; a bin subset's spans the whole sinogram
+  ctx->max_subset_bins = g.subset_kind == SPDHG_SUBSETS_BINS
+                             ? ctx->M
+                             : (int64_t)((g.n_views + g.n_subsets - 1) / g.n_subsets) * g.n_radial * P;
+  if (g.subset_kind == SPDHG_SUBSETS_BINS && ctx->M < g.n_subsets) {
+    delete ctx;
+    return SPDHG_ERR_ARG;
+  }
 
   // device tables (FP64 on the host, stored as double-float pairs hi + lo)
   const double pi = 3.14159265358979323846;
@@ -454,13 +463,34 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   std::vector<SegDev> seg(S);
   std::vector<int> plane_seg(P);
   int p0 = 0;
+  int fz_lo = taps - 1, fz_stride = g.nz;
   for (int k = 0; k < S; ++k) {
     seg[k].p0 = p0;
     seg[k].n = g.seg_n[k];
-    split((g.seg_zmid0[k] - loz) / g.vz, seg[k].f_hi, seg[k].f_lo);
+    const double f = (g.seg_zmid0[k] - loz) / g.vz;
+    split(f, seg[k].f_hi, seg[k].f_lo);
+    // Axial bound of the forward gather: along the LOR of plane 0 the slab coordinate is
+    // f + kappa t with |t| <= h, so every slab it touches lies in [floor(f - |kappa| h),
+    // floor(f + |kappa| h)]; the tap offset j0 (plane 0's top slab is -j0) lies within that range
+    // widened by two slabs for rounding.  The staged columns get frames that hold every read.
+    double zlo = f, zhi = f;
+    for (int r = 0; r < R; ++r) {
+      const double s_r = (r - 0.5 * (R - 1)) * g.d_radial;
+      const double h = sqrt(g.radius * g.radius - s_r * s_r);
+      const double span = fabs(g.seg_dz[k]) / (2.0 * h) * h / g.vz;  // |kappa| h in slabs
+      zlo = std::min(zlo, f - span);
+      zhi = std::max(zhi, f + span);
+    }
+    seg[k].jlo = -(int)floor(zhi) - 2;
+    seg[k].jhi = -(int)floor(zlo) + 2;
+    fz_lo = std::max(fz_lo, seg[k].jhi + taps - 1);
     for (int q = 0; q < g.seg_n[k]; ++q) plane_seg[p0 + q] = k;
     p0 += g.seg_n[k];
   }
+  // plane q (read as min(q, n - 1)) reads slabs q - j0 - t: the highest is n - 1 - jlo
+  for (int k = 0; k < S; ++k) fz_stride = std::max(fz_stride, g.seg_n[k] + 3 - seg[k].jlo);
+  fz_stride += fz_lo;
+  fz_stride = std::max(fz_stride, fz_lo + g.nz);
   std::vector<int2> runs;
   for (int k = 0; k < S; ++k)
     for (int q0 = 0; q0 < g.seg_n[k]; q0 += 32) runs.push_back(make_int2(k, q0));
@@ -492,6 +522,7 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   d.V = V;
   d.P = P;
   d.m = g.n_subsets;
+  d.bins = g.subset_kind == SPDHG_SUBSETS_BINS ? 1 : 0;
   d.n_seg = S;
   d.taps = taps;
   d.nr_max = nr_max;
@@ -505,6 +536,8 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   d.plane_seg = ctx->d_plane_seg;
   d.n_runs = (int)runs.size();
   d.runs = ctx->d_runs;
+  d.fz_lo = fz_lo;
+  d.fz_stride = fz_stride;
   *out = ctx;
   return SPDHG_OK;
 }
@@ -513,7 +546,7 @@ void spdhg_destroy(spdhg_ctx* ctx) {
   if (!ctx) return;
   void* ptrs[] = {ctx->d_view, ctx->d_view_inv, ctx->d_rad, ctx->d_rs, ctx->d_runs, ctx->d_seg, ctx->d_plane_seg, ctx->b, ctx->r, ctx->mult, ctx->side,
                   ctx->x[0], ctx->x[1], ctx->z, ctx->T, ctx->y, ctx->sigma, ctx->wdy, ctx->q[0], ctx->q[1],
-                  ctx->w[0], ctx->w[1], ctx->zw, ctx->q2[0], ctx->q2[1], ctx->tgv_b, ctx->tmp_sino, ctx->tmp_img, ctx->fwd_part, ctx->fwd_tickets,
+                  ctx->w[0], ctx->w[1], ctx->zw, ctx->q2[0], ctx->q2[1], ctx->tgv_b, ctx->tmp_sino, ctx->tmp_img, ctx->tmp_img2, ctx->em_sens, ctx->fwd_part, ctx->fwd_tickets,
                   ctx->red, ctx->red_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -575,6 +608,7 @@ int spdhg_set_data(spdhg_ctx* ctx, const float* b, const float* r, const float* 
   }
   ctx->has_data = true;
   ctx->is_setup = false;
+  ctx->em_sens_kind = -1;  // sensitivities follow the multipliers
   ++ctx->graph_gen;  // mult may have switched between a buffer and none
   return SPDHG_OK;
 }
@@ -679,8 +713,22 @@ int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int
     CK(dalloc(&ctx->q2[1], 6 * N));
   }
 
+  if (p.sampling == SPDHG_SAMPLING_CUSTOM) {
+    if (!p.probs) return fail(ctx, SPDHG_ERR_ARG, "custom sampling needs params.probs");
+    const int nb = m + n_prior_blocks(p.prior);
+    double tot = 0.0;
+    for (int i = 0; i < nb; ++i) {
+      if (!(p.probs[i] > 0.0) || !isfinite(p.probs[i])) return fail(ctx, SPDHG_ERR_ARG, "custom probabilities must be positive");
+      tot += p.probs[i];
+    }
+    if (fabs(tot - 1.0) > 1e-9) return fail(ctx, SPDHG_ERR_ARG, "custom probabilities must sum to one");
+  } else if (p.sampling != SPDHG_SAMPLING_BALANCED && p.sampling != SPDHG_SAMPLING_UNIFORM) {
+    return fail(ctx, SPDHG_ERR_ARG, "unknown sampling");
+  }
   ctx->params = p;
+  ctx->params.probs = nullptr;  // the caller's array is not kept
   ctx->probs = block_probs(m, p.prior, p.sampling);
+  if (p.sampling == SPDHG_SAMPLING_CUSTOM) ctx->probs.assign(p.probs, p.probs + ctx->probs.size());
   const double gn = grad_norm(ctx->geom.nx, ctx->geom.ny, ctx->geom.nz);
 
   // scalar data steps (Eq. EQU:STEPSIZE:SCALAR): sigma_i = gamma rho / ||P_i||, T_i = rho p_i /
@@ -705,12 +753,7 @@ int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int
     CK(cudaGetLastError());
   }
   for (int i = 0; i < (p.precond ? m : 0); ++i) {
-    if (ctx->has_mult) {
-      CK(launch_gather_subset(ctx->dg, i, ctx->mult, nullptr, ctx->wdy, s));
-    } else {
-      k_fill<<<grid_for(ctx->max_subset_bins), 256, 0, s>>>(ctx->wdy, ctx->max_subset_bins, 1.f);
-      CK(cudaGetLastError());
-    }
+    CK(launch_gather_subset(ctx->dg, i, nullptr, ctx->has_mult ? ctx->mult : nullptr, ctx->wdy, s));
     BwdArgs a{};
     a.w = ctx->wdy;
     a.T = ctx->T;
@@ -734,7 +777,16 @@ int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int
   CK(cudaGetLastError());
   // sigma_j = gamma rho / (P 1)_j for every bin (Eq. EQU:STEPSIZE:PRECOND), stored once; scalar
   // steps: gamma rho / ||P_i|| on every bin of subset i
-  if (!p.precond) {
+  if (!p.precond && ctx->dg.bins) {
+    std::vector<float> sig_i(m);
+    for (int i = 0; i < m; ++i) sig_i[i] = norms[i] > 0.0 ? (float)(p.gamma * p.rho / norms[i]) : 0.f;
+    CK(dalloc(&ctx->tmp_img, N));  // m <= N floats of per-subset steps
+    if (m > N) return fail(ctx, SPDHG_ERR_UNSUPPORTED, "more bin subsets than voxels");
+    CK(cudaMemcpyAsync(ctx->tmp_img, sig_i.data(), m * sizeof(float), cudaMemcpyHostToDevice, s));
+    k_fill_bins<<<grid_for(M), 256, 0, s>>>(ctx->sigma, M, m, ctx->tmp_img);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+  } else if (!p.precond) {
     const int64_t RP = (int64_t)ctx->dg.R * ctx->dg.P;
     for (int v = 0; v < ctx->dg.V; ++v) {
       const double nrm = norms[v % m];
@@ -924,6 +976,107 @@ int spdhg_objective(spdhg_ctx* ctx, const float* x, int where, double out[3], vo
   return SPDHG_OK;
 }
 
+int spdhg_psnr(spdhg_ctx* ctx, const float* x, const float* x_star, int where, double* out, void* stream) {
+  if (!ctx || !x_star || !out || (where != SPDHG_WHERE_HOST && where != SPDHG_WHERE_DEVICE)) return SPDHG_ERR_ARG;
+  if (int st = check_device(ctx)) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = ctx->N;
+  const float* xd = x;
+  const float* xs = x_star;
+  if (!x) {
+    if (!ctx->is_setup) return fail(ctx, SPDHG_ERR_STATE, "no iterate before spdhg_setup");
+    xd = ctx->x[ctx->xcur];
+  } else if (where == SPDHG_WHERE_HOST) {
+    CK(dalloc(&ctx->tmp_img2, N));
+    CK(cudaMemcpyAsync(ctx->tmp_img2, x, N * sizeof(float), cudaMemcpyHostToDevice, s));
+    xd = ctx->tmp_img2;
+  }
+  if (where == SPDHG_WHERE_HOST) {
+    CK(dalloc(&ctx->tmp_img, N));
+    CK(cudaMemcpyAsync(ctx->tmp_img, x_star, N * sizeof(float), cudaMemcpyHostToDevice, s));
+    xs = ctx->tmp_img;
+  }
+  CK(launch_psnr_terms(xd, xs, N, ctx->red, ctx->red_blocks, ctx->red_out + 4, s));
+  double h[2] = {0, 0};
+  CK(cudaMemcpyAsync(h, ctx->red_out + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  // PSNR(x, x*) = 20 log10(||x*||_inf / ||x - x*||_2)  (Sec. 4, log read as base 10)
+  *out = 20.0 * log10(h[1] / sqrt(h[0]));
+  return SPDHG_OK;
+}
+
+}  // extern "C"
+
+int spdhg::runlog_begin(spdhg_ctx* ctx, const spdhg_params& p, spdhg_report* rep, RunLog& L, cudaStream_t s) {
+  const bool target = p.target_gap > 0.0;
+  if (target && !isfinite(p.psi_star)) return fail(ctx, SPDHG_ERR_ARG, "target_gap needs a finite psi_star");
+  if (p.x_star) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, p.x_star) != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+      cudaGetLastError();
+      return fail(ctx, SPDHG_ERR_ARG, "x_star must be device memory");
+    }
+  }
+  L = RunLog{};
+  L.every = p.objective_every > 0 ? p.objective_every : ((target || p.x_star) ? 1 : 0);
+  if (rep) {
+    rep->epochs_done = 0;
+    rep->iterations_done = 0;
+    rep->stop_epoch = -1;
+    rep->ms_to_stop = NAN;
+    rep->psi_zero = NAN;
+    if (rep->objective)
+      for (int e = 0; e <= p.epochs; ++e) rep->objective[e] = NAN;
+    if (rep->psnr)
+      for (int e = 0; e <= p.epochs; ++e) rep->psnr[e] = NAN;
+  }
+  if (target) {
+    // Psi(0): the zero image, for the normaliser of every run (warm starts included)
+    CK(dalloc(&ctx->tmp_img, ctx->N));
+    CK(cudaMemsetAsync(ctx->tmp_img, 0, ctx->N * sizeof(float), s));
+    double o[3];
+    if (int st = spdhg_objective(ctx, ctx->tmp_img, SPDHG_WHERE_DEVICE, o, s)) return st;
+    L.psi0 = o[2];
+    if (rep) rep->psi_zero = o[2];
+  }
+  if (rep && rep->objective && L.every > 0) {
+    double o[3];
+    if (int st = spdhg_objective(ctx, nullptr, SPDHG_WHERE_DEVICE, o, s)) return st;
+    rep->objective[0] = o[2];
+  }
+  if (rep && rep->psnr && p.x_star) {
+    double v;
+    if (int st = spdhg_psnr(ctx, nullptr, p.x_star, SPDHG_WHERE_DEVICE, &v, s)) return st;
+    rep->psnr[0] = v;
+  }
+  return SPDHG_OK;
+}
+
+int spdhg::runlog_epoch(spdhg_ctx* ctx, const spdhg_params& p, spdhg_report* rep, RunLog& L, int e, double epoch_ms,
+                        cudaStream_t s) {
+  L.ms += epoch_ms;
+  if (L.every <= 0 || e % L.every) return SPDHG_OK;
+  double o[3];
+  if (int st = spdhg_objective(ctx, nullptr, SPDHG_WHERE_DEVICE, o, s)) return st;
+  if (rep && rep->objective) rep->objective[e] = o[2];
+  if (!isfinite(o[2])) return fail(ctx, SPDHG_ERR_DIVERGED, "objective is not finite");
+  if (rep && rep->psnr && p.x_star) {
+    double v;
+    if (int st = spdhg_psnr(ctx, nullptr, p.x_star, SPDHG_WHERE_DEVICE, &v, s)) return st;
+    rep->psnr[e] = v;
+  }
+  if (p.target_gap > 0.0 && (o[2] - p.psi_star) <= p.target_gap * (L.psi0 - p.psi_star)) {
+    L.stopped = true;
+    if (rep) {
+      rep->stop_epoch = e;
+      rep->ms_to_stop = L.ms;
+    }
+  }
+  return SPDHG_OK;
+}
+
+extern "C" {
+
 int spdhg_run(spdhg_ctx* ctx, const spdhg_params* params, float* x_inout, int where, spdhg_report* rep,
               void* stream) {
   if (!ctx || !params || params->epochs < 0) return SPDHG_ERR_ARG;
@@ -938,47 +1091,135 @@ int spdhg_run(spdhg_ctx* ctx, const spdhg_params* params, float* x_inout, int wh
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  int status = SPDHG_OK;
-  const int every = params->objective_every;
-  if (rep) {
-    rep->epochs_done = 0;
-    rep->iterations_done = 0;
-    if (rep->objective)
-      for (int e = 0; e <= params->epochs; ++e) rep->objective[e] = NAN;
-  }
-  if (rep && rep->objective && every > 0) {
-    double o[3];
-    if ((status = spdhg_objective(ctx, nullptr, SPDHG_WHERE_DEVICE, o, stream))) goto done;
-    rep->objective[0] = o[2];
-  }
-  for (int ep = 0; ep < params->epochs; ++ep) {
+  RunLog L;
+  int status = runlog_begin(ctx, *params, rep, L, s);
+  const bool timed = (rep && rep->epoch_ms) || params->target_gap > 0.0;
+  for (int ep = 0; ep < params->epochs && status == SPDHG_OK; ++ep) {
     spdhg_sample(ctx->params.seed, (uint64_t)ep * ipe, ipe, ctx->probs.data(), (int)ctx->probs.size(), seq.data());
-    if (cudaEventRecord(e0, s) != cudaSuccess) { status = fail(ctx, SPDHG_ERR_CUDA, "event record"); goto done; }
-    if ((status = spdhg_iterate(ctx, seq.data(), ipe, stream))) goto done;
-    if (cudaEventRecord(e1, s) != cudaSuccess) { status = fail(ctx, SPDHG_ERR_CUDA, "event record"); goto done; }
-    if (rep && rep->epoch_ms) {
-      float ms = 0.f;
+    if (cudaEventRecord(e0, s) != cudaSuccess) { status = fail(ctx, SPDHG_ERR_CUDA, "event record"); break; }
+    if ((status = spdhg_iterate(ctx, seq.data(), ipe, stream))) break;
+    if (cudaEventRecord(e1, s) != cudaSuccess) { status = fail(ctx, SPDHG_ERR_CUDA, "event record"); break; }
+    float ms = 0.f;
+    if (timed) {
       cudaEventSynchronize(e1);
       cudaEventElapsedTime(&ms, e0, e1);
-      rep->epoch_ms[ep] = ms;
+      if (rep && rep->epoch_ms) rep->epoch_ms[ep] = ms;
     }
     if (rep) {
       rep->epochs_done = ep + 1;
       rep->iterations_done = (int64_t)(ep + 1) * ipe;
     }
-    if (every > 0 && (ep + 1) % every == 0) {
-      double o[3];
-      if ((status = spdhg_objective(ctx, nullptr, SPDHG_WHERE_DEVICE, o, stream))) goto done;
-      if (rep && rep->objective) rep->objective[ep + 1] = o[2];
-      if (!isfinite(o[2])) { status = fail(ctx, SPDHG_ERR_DIVERGED, "objective is not finite"); goto done; }
-    }
+    if ((status = runlog_epoch(ctx, *params, rep, L, ep + 1, ms, s))) break;
+    if (L.stopped) break;
   }
-  if (x_inout) status = copy_out(ctx, x_inout, ctx->x[ctx->xcur], ctx->N, where, s);
+  if (status == SPDHG_OK && x_inout) status = copy_out(ctx, x_inout, ctx->x[ctx->xcur], ctx->N, where, s);
   if (status == SPDHG_OK) {
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) status = fail(ctx, SPDHG_ERR_CUDA, cudaGetErrorString(e));
   }
-done:
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return status;
+}
+
+int spdhg_osem(spdhg_ctx* ctx, const spdhg_params* params, int mlem, float* x_inout, int where, spdhg_report* rep,
+               void* stream) {
+  if (!ctx || !params || params->epochs < 0 || (x_inout && where != SPDHG_WHERE_HOST && where != SPDHG_WHERE_DEVICE))
+    return SPDHG_ERR_ARG;
+  if (int st = check_device(ctx)) return st;
+  if (!ctx->has_data) return fail(ctx, SPDHG_ERR_STATE, "spdhg_set_data must be called before spdhg_osem");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t N = ctx->N;
+  const int m = mlem ? 1 : ctx->geom.n_subsets;
+  CK(dalloc(&ctx->x[0], N));
+  CK(dalloc(&ctx->x[1], N));
+  CK(dalloc(&ctx->wdy, mlem ? ctx->M : ctx->max_subset_bins));
+  if (mlem && ctx->max_subset_bins < ctx->M) {
+    // MLEM needs a full-size ratio sinogram
+    CK(dalloc(&ctx->tmp_sino, ctx->M));
+  }
+  float* ratio = (mlem && ctx->max_subset_bins < ctx->M) ? ctx->tmp_sino : ctx->wdy;
+  // sensitivity images P_i^T 1 (Eq. EQU:OSEM), or P^T 1 (Eq. EQU:MLEM)
+  const int kind = mlem ? 1 : 0;
+  if (ctx->em_sens_kind != kind) {
+    if (ctx->em_sens) cudaFree(ctx->em_sens);
+    ctx->em_sens = nullptr;
+    ctx->em_sens_kind = -1;
+    CK(cudaMalloc(&ctx->em_sens, (size_t)m * N * sizeof(float)));
+    for (int i = 0; i < m; ++i) {
+      const int sub = mlem ? -1 : i;
+      CK(launch_gather_subset(ctx->dg, sub, nullptr, ctx->has_mult ? ctx->mult : nullptr, ratio, s));
+      BwdArgs a{};
+      a.w = ratio;
+      a.out = ctx->em_sens + (size_t)i * N;
+      CK(launch_backward(ctx->dg, sub, BWD_OUT, a, s));
+    }
+    ctx->em_sens_kind = kind;
+  }
+  // the iterate: u0 from the caller, or ones (Eq. EQU:MLEM needs a positive start)
+  float* u = ctx->x[0];
+  ctx->xcur = 0;
+  if (x_inout) {
+    if (int st = copy_in(ctx, u, x_inout, N, where, s)) return st;
+  } else {
+    k_fill<<<grid_for(N), 256, 0, s>>>(u, N, 1.f);
+    CK(cudaGetLastError());
+  }
+  // the objective of an EM run is the data term alone
+  spdhg_params p = *params;
+  p.prior = SPDHG_PRIOR_NONE;
+  p.probs = nullptr;
+  ctx->params = p;
+  ctx->is_setup = true;
+  ++ctx->graph_gen;
+  ctx->probs = block_probs(ctx->geom.n_subsets, SPDHG_PRIOR_NONE, SPDHG_SAMPLING_UNIFORM);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  RunLog L;
+  int status = runlog_begin(ctx, p, rep, L, s);
+  const bool timed = (rep && rep->epoch_ms) || p.target_gap > 0.0;
+  for (int ep = 0; ep < p.epochs && status == SPDHG_OK; ++ep) {
+    if (cudaEventRecord(e0, s) != cudaSuccess) { status = fail(ctx, SPDHG_ERR_CUDA, "event record"); break; }
+    for (int k = 0; k < m && status == SPDHG_OK; ++k) {
+      const int sub = mlem ? -1 : k;  // i = k mod m (Eq. EQU:OSEM)
+      FwdArgs fa{};
+      fa.x = u;
+      fa.mult = ctx->has_mult ? ctx->mult : nullptr;
+      fa.b = ctx->b;
+      fa.r = ctx->r;
+      fa.wdy = ratio;
+      if ((status = prepare_forward(ctx, sub, fa, s))) break;
+      cudaError_t e = launch_forward(ctx->dg, sub, FWD_EM, fa, s);
+      if (e == cudaSuccess) {
+        BwdArgs ba{};
+        ba.w = ratio;
+        ba.x = u;
+        ba.T = ctx->em_sens + (size_t)(mlem ? 0 : k) * N;
+        e = launch_backward(ctx->dg, sub, BWD_EM, ba, s);
+      }
+      if (e != cudaSuccess) status = fail(ctx, SPDHG_ERR_CUDA, std::string("EM iteration: ") + cudaGetErrorString(e));
+    }
+    if (status) break;
+    if (cudaEventRecord(e1, s) != cudaSuccess) { status = fail(ctx, SPDHG_ERR_CUDA, "event record"); break; }
+    float ms = 0.f;
+    if (timed) {
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep && rep->epoch_ms) rep->epoch_ms[ep] = ms;
+    }
+    if (rep) {
+      rep->epochs_done = ep + 1;
+      rep->iterations_done = (int64_t)(ep + 1) * m;
+    }
+    if ((status = runlog_epoch(ctx, p, rep, L, ep + 1, ms, s))) break;
+    if (L.stopped) break;
+  }
+  if (status == SPDHG_OK && x_inout) status = copy_out(ctx, x_inout, u, N, where, s);
+  if (status == SPDHG_OK) {
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) status = fail(ctx, SPDHG_ERR_CUDA, cudaGetErrorString(e));
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return status;
@@ -1001,10 +1242,8 @@ int spdhg_tune(spdhg_ctx* ctx, int knob, int value) {
       if (value > 16) return fail(ctx, SPDHG_ERR_ARG, "forward split out of range");
       break;
     case SPDHG_TUNE_FWD_WARPS:
-      if (value != 0 && value != 4 && value != 8 && value != 16)
-        return fail(ctx, SPDHG_ERR_ARG, "forward warps must be 4, 8 or 16");
-      if (value != 0 && (ctx->dg.n_runs + value - 1) / value > 4)
-        return fail(ctx, SPDHG_ERR_ARG, "too few forward warps for the planes of a line");
+      if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+        return fail(ctx, SPDHG_ERR_ARG, "forward warps must be 1, 2, 4, 8 or 16");
       break;
     default: break;
   }

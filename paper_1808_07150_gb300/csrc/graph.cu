@@ -308,6 +308,7 @@ extern "C" int spdhg_run_batch(spdhg_ctx* const* ctxs, const spdhg_params* param
   cudaStream_t s = (cudaStream_t)stream;
   EpochGraph eg;
   eg.br.resize(n);
+  std::vector<RunLog> logs(n);
   int epochs = 0;
   for (int r = 0; r < n; ++r) {
     spdhg_ctx* ctx = ctxs[r];
@@ -316,38 +317,29 @@ extern "C" int spdhg_run_batch(spdhg_ctx* const* ctxs, const spdhg_params* param
     eg.br[r].ctx = ctx;
     eg.br[r].ipe = iterations_per_epoch(ctx);
     epochs = std::max(epochs, params[r].epochs);
-    if (reports) {
-      reports[r].epochs_done = 0;
-      reports[r].iterations_done = 0;
-      if (reports[r].objective)
-        for (int e = 0; e <= params[r].epochs; ++e) reports[r].objective[e] = NAN;
-    }
+    if (int st = runlog_begin(ctx, params[r], reports ? &reports[r] : nullptr, logs[r], s)) return st;
   }
   if (int st = build(eg, ctxs[0])) return st;
   std::vector<cudaEvent_t> ev(2 * (size_t)epochs, nullptr);
   int status = SPDHG_OK;
   std::vector<int32_t> seq;
-  auto objective = [&](int r, int e) -> int {
-    const int every = params[r].objective_every;
-    if (every <= 0 || e % every) return SPDHG_OK;
-    double o[3];
-    if (int st = spdhg_objective(ctxs[r], nullptr, SPDHG_WHERE_DEVICE, o, stream)) return st;
-    if (reports && reports[r].objective) reports[r].objective[e] = o[2];
-    if (e > 0 && !isfinite(o[2])) return fail(ctxs[r], SPDHG_ERR_DIVERGED, "objective is not finite");
-    return SPDHG_OK;
-  };
-  for (int r = 0; r < n && status == SPDHG_OK; ++r)
-    if (reports && reports[r].objective) status = objective(r, 0);  // as spdhg_run: logged start only
+  auto active = [&](int r, int e) { return e < params[r].epochs && !logs[r].stopped; };
+  bool timed_now = false;
+  for (int r = 0; r < n; ++r) timed_now = timed_now || params[r].target_gap > 0.0;
+  std::vector<int> ran(n, 0);  // epochs each context has run
   for (int e = 0; e < epochs && status == SPDHG_OK; ++e) {
+    bool any = false;
+    for (int r = 0; r < n; ++r) any = any || active(r, e);
+    if (!any) break;  // every context has finished or reached its target
     for (int r = 0; r < n && status == SPDHG_OK; ++r) {
       Branch& b = eg.br[r];
-      const bool active = e < params[r].epochs;
-      if (active) {
+      const bool act = active(r, e);
+      if (act) {
         seq.resize(b.ipe);
         spdhg_sample(b.ctx->params.seed, (uint64_t)e * b.ipe, b.ipe, b.ctx->probs.data(), (int)b.ctx->probs.size(),
                      seq.data());
       }
-      status = update(eg, b, active ? seq.data() : nullptr);
+      status = update(eg, b, act ? seq.data() : nullptr);
     }
     if (status) break;
     for (int k = 0; k < 2 && status == SPDHG_OK; ++k)
@@ -357,13 +349,20 @@ extern "C" int spdhg_run_batch(spdhg_ctx* const* ctxs, const spdhg_params* param
     cudaError_t le = cudaGraphLaunch(eg.exec, s);
     if (le != cudaSuccess) { status = fail(ctxs[0], SPDHG_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(le)); break; }
     cudaEventRecord(ev[2 * e + 1], s);
+    // the epoch's device time is read now only when a stopping rule needs it; otherwise the host
+    // goes on preparing the next epoch while this one runs, and the times are read at the end
+    float ms = 0.f;
+    if (timed_now && (cudaEventSynchronize(ev[2 * e + 1]) != cudaSuccess ||
+                      cudaEventElapsedTime(&ms, ev[2 * e], ev[2 * e + 1]) != cudaSuccess))
+      ms = NAN;
     for (int r = 0; r < n && status == SPDHG_OK; ++r) {
-      if (e >= params[r].epochs) continue;
+      if (!active(r, e)) continue;
+      ran[r] = e + 1;
       if (reports) {
         reports[r].epochs_done = e + 1;
         reports[r].iterations_done = (int64_t)(e + 1) * eg.br[r].ipe;
       }
-      status = objective(r, e + 1);
+      status = runlog_epoch(ctxs[r], params[r], reports ? &reports[r] : nullptr, logs[r], e + 1, ms, s);
     }
   }
   if (status == SPDHG_OK) {
@@ -372,10 +371,11 @@ extern "C" int spdhg_run_batch(spdhg_ctx* const* ctxs, const spdhg_params* param
   }
   if (status == SPDHG_OK && reports) {
     for (int e = 0; e < epochs; ++e) {
+      if (!ev[2 * e]) break;
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, ev[2 * e], ev[2 * e + 1]) != cudaSuccess) ms = NAN;
       for (int r = 0; r < n; ++r)
-        if (reports[r].epoch_ms && e < params[r].epochs) reports[r].epoch_ms[e] = ms;
+        if (reports[r].epoch_ms && e < ran[r]) reports[r].epoch_ms[e] = ms;
     }
   }
   for (cudaEvent_t x : ev)

@@ -13,7 +13,6 @@ namespace spdhg {
 
 constexpr int kMaxSeg = 32;       // segments held in the per-line shared tables
 constexpr int kMaxTaps = 4;       // slices an oblique LOR may cross inside one transaxial pixel
-constexpr int kMaxPlanesPerThread = 4;
 
 // Per-segment constants.  Plane q of segment g has its LOR mid-point at slab coordinate
 // f + q (in units of vz measured from the lower image face, so slab iz is [iz, iz+1)); f is
@@ -22,6 +21,7 @@ struct SegDev {
   int p0;      // first plane index of the segment in the sinogram
   int n;       // planes in the segment
   float f_hi, f_lo;
+  int jlo, jhi;  // range of the tap offset j0 of any pixel of any LOR of the segment (host bound)
 };
 
 // Geometry passed by value to every kernel.  Transaxial quantities are in pixel units (mm / vx);
@@ -30,6 +30,7 @@ struct SegDev {
 struct DevGeom {
   int nx, ny, nz;
   int R, V, P, m;        // radial bins, views, planes, subsets
+  int bins;              // 1: bin-interleaved subsets (every subset spans all views), 0: view subsets
   int n_seg;
   int taps;              // maximum slices a LOR crosses inside one pixel
   int nr_max;            // maximum candidate radial bins per pixel and view
@@ -41,8 +42,10 @@ struct DevGeom {
   const float4* rs;      // per (radial bin, segment): kappa_hi, kappa_lo, len_scale, 0
   const SegDev* seg;
   const int* plane_seg;  // plane -> segment
-  int n_runs;            // warp-sized plane runs: run k = planes [q0, q0 + 32) of one segment
-  const int2* runs;      // (segment, q0) per run
+  int n_runs;            // plane runs of the forward projector: run k = planes [q0, q0 + 32) of one segment
+  const int2* runs;      // (segment, q0) per run, segment-major
+  int fz_lo;             // forward staging: zero slabs below each staged x column
+  int fz_stride;         // forward staging: floats per staged x column (frames included)
   int tune[SPDHG_TUNE_KNOBS];  // launch-shape overrides (0: built-in heuristic)
 };
 
@@ -58,12 +61,24 @@ cudaError_t allow_dynamic_smem(K kern, size_t smem) {
   return allow_dynamic_smem_fn(reinterpret_cast<const void*>(kern), smem);
 }
 
-// Views of subset i: i, i+m, ...  (subset < 0: all views).
+// Proximal map of the non-negativity constraint, max(v, 0) (Sec. 2.2, the Example after the prox
+// definition), written so that a
+// NaN stays NaN: fmaxf(NaN, 0) would return 0 and hide a state that has stopped being finite
+// from the objective check that reports divergence.
+__host__ __device__ __forceinline__ float prox_nonneg(float v) { return v < 0.f ? 0.f : v; }
+
+// Views a subset's projection traverses: i, i+m, ... for view subsets; every view for bin
+// subsets and for subset < 0 (all bins).
 __host__ __device__ inline int subset_views(const DevGeom& g, int subset) {
-  return subset < 0 ? g.V : (g.V - subset + g.m - 1) / g.m;
+  return (subset < 0 || g.bins) ? g.V : (g.V - subset + g.m - 1) / g.m;
 }
 __host__ __device__ inline int subset_view(const DevGeom& g, int subset, int l) {
-  return subset < 0 ? l : subset + l * g.m;
+  return (subset < 0 || g.bins) ? l : subset + l * g.m;
+}
+// Whether bin j (flattened sinogram index) belongs to `subset` (always for view subsets, whose
+// traversal already visits only their views, and for subset < 0).
+__host__ __device__ inline bool bin_in_subset(const DevGeom& g, int subset, size_t j) {
+  return subset < 0 || !g.bins || (int)(j % (size_t)g.m) == subset;
 }
 
 struct Ctx;
@@ -71,8 +86,8 @@ struct Ctx;
 // ---------------------------------------------------------------------------------------
 // projector launches (projector.cu)
 // ---------------------------------------------------------------------------------------
-enum FwdMode { FWD_PROJECT = 0, FWD_SIGMA = 1, FWD_DATA = 2 };
-enum BwdMode { BWD_OUT = 0, BWD_SENS = 1, BWD_UPDATE = 2 };
+enum FwdMode { FWD_PROJECT = 0, FWD_SIGMA = 1, FWD_DATA = 2, FWD_EM = 3 };
+enum BwdMode { BWD_OUT = 0, BWD_SENS = 1, BWD_UPDATE = 2, BWD_EM = 3 };
 
 struct FwdArgs {
   const float* x;        // image
@@ -82,32 +97,34 @@ struct FwdArgs {
   const float* b;
   const float* r;
   float* y;              // dual, full sinogram
-  float* wdy;            // subset-local mult * (y+ - y)
+  float* wdy;            // subset-local mult * (y+ - y); FWD_EM: mult * b / (P x + r)
   const float* sigma;    // FWD_DATA: per-bin dual step sigma_j (full sinogram)
   float gamma_rho;       // gamma * rho
   // row-split scratch: partial plane sums [line][part][P] and one ticket per line (zeroed)
   float* part_acc;
-  float* part_chord;
   unsigned* tickets;
   size_t part_cap;       // floats in each partial buffer
-  size_t ticket_cap;     // tickets
+  size_t ticket_cap;     // tickets (one per line and plane part)
 };
-// blocks per LOR line the forward projector uses for `subset` (1: no scratch needed)
+// row parts per LOR line the forward projector uses for `subset` (1: no scratch needed)
 int forward_split(const DevGeom& g, int subset);
+// plane parts per LOR line (blocks that share the rows of a line, each with its own planes)
+int forward_parts(const DevGeom& g);
 
 struct BwdArgs {
   const float* w;        // subset-local sinogram (mult already applied)
   float* out;            // BWD_OUT: image (overwritten)
-  float* T;              // BWD_SENS: running min; BWD_UPDATE: step image
+  float* T;              // BWD_SENS: running min; BWD_UPDATE: step image; BWD_EM: sensitivity P_i^T 1
   float sens_num;        // BWD_SENS: rho p_i / gamma
-  float* x;              // BWD_UPDATE
+  float* x;              // BWD_UPDATE, BWD_EM
   float* z;
   float inv_p;
 };
 
 cudaError_t launch_forward(const DevGeom& g, int subset, int mode, const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_backward(const DevGeom& g, int subset, int mode, const BwdArgs& a, cudaStream_t s);
-// w_local = mult * y over the bins of subset i (mult may be null)
+// w_local = y * mult over the bins of subset i (y or mult null: ones); for bin subsets the
+// buffer spans the whole sinogram and the other subsets' bins are 0
 cudaError_t launch_gather_subset(const DevGeom& g, int subset, const float* y, const float* mult,
                                  float* w_local, cudaStream_t s);
 
@@ -155,6 +172,9 @@ cudaError_t launch_side_max_grad(const DevGeom& g, const float* side, double* pa
 // *out = sum_j v_j^2 (FP64, deterministic);  v = y / sqrt(*ss)
 cudaError_t launch_sumsq(const float* v, int64_t n, double* partial, int nblocks, double* out, cudaStream_t s);
 cudaError_t launch_normalize(const float* y, int64_t n, const double* ss, float* v, cudaStream_t s);
+// out[0] = sum (x - xs)^2, out[1] = max |xs| (FP64); `partial` holds 2 * nblocks doubles
+cudaError_t launch_psnr_terms(const float* x, const float* xs, int64_t n, double* partial, int nblocks,
+                              double* out, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------
 // iteration driver (api.cu) and epoch graphs (graph.cu)
@@ -167,6 +187,20 @@ int forward_scratch(spdhg_ctx* ctx, int subset, FwdArgs& a, cudaStream_t s);
 int prepare_all_forward(spdhg_ctx* ctx, cudaStream_t s);
 struct GraphCache;
 void graph_cache_free(spdhg_ctx* ctx);
+
+// Quality log and stopping rule shared by spdhg_run and spdhg_run_batch: the relative objective
+// (Psi(x^k) - Psi*) / (Psi(0) - Psi*) and PSNR(x^k, x*) of Sec. 4, evaluated in FP64 on the GPU.
+struct RunLog {
+  int every = 0;         // evaluate after every `every` epochs (0: never)
+  double psi0 = 0.0;     // Psi(0), when a target gap is set
+  double ms = 0.0;       // solver device time so far
+  bool stopped = false;  // the target gap was reached
+};
+// after spdhg_setup: fills the report's defaults and evaluates the start (index 0)
+int runlog_begin(spdhg_ctx* ctx, const spdhg_params& p, spdhg_report* rep, RunLog& L, cudaStream_t s);
+// after epoch e (1-based) that took epoch_ms of device time
+int runlog_epoch(spdhg_ctx* ctx, const spdhg_params& p, spdhg_report* rep, RunLog& L, int e, double epoch_ms,
+                 cudaStream_t s);
 
 }  // namespace spdhg
 
@@ -206,7 +240,10 @@ struct spdhg_ctx {
   float Tw = 0.f;
   // scratch
   float* tmp_sino = nullptr;   // M floats (objective, sigma export)
-  float* tmp_img = nullptr;    // N floats (objective of a host image)
+  float* tmp_img = nullptr;    // N floats (objective of a host image, Psi(0), x* of spdhg_psnr)
+  float* tmp_img2 = nullptr;   // N floats (x of spdhg_psnr from the host)
+  float* em_sens = nullptr;    // OSEM / MLEM sensitivity images P_i^T 1 (m x N, or N for MLEM)
+  int em_sens_kind = -1;       // which set em_sens holds: 0 OSEM, 1 MLEM, -1 none (reset by set_data)
   float* fwd_part = nullptr;   // forward row-split partial sums (2 x fwd_part_cap floats)
   unsigned* fwd_tickets = nullptr;
   size_t fwd_part_cap = 0, fwd_ticket_cap = 0;

@@ -5,8 +5,6 @@
 // cudaFree would synchronise the device.  spdhg_backproject keeps its gathered sinogram in a
 // buffer the context allocates on first use; this variant keeps that scratch in a fixed
 // file-scope device array instead, so the call itself allocates nothing.
-#include <mutex>
-
 #include "internal.cuh"
 
 using namespace spdhg;
@@ -18,22 +16,14 @@ namespace {
 constexpr int64_t kNoallocScratchFloats = int64_t(1) << 21;
 static __device__ __align__(256) float g_noalloc_scratch[kNoallocScratchFloats];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-float* g_addr[kMaxDevices] = {nullptr};
-
 // Device address of the scratch array on the current device (host code only sees a stand-in
-// symbol).  Looked up once per device, with that device current.
-cudaError_t scratch_address(int dev, float** out) {
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<float*>(p);
-  }
-  *out = g_addr[dev];
+// symbol).  Looked up on every call, with the context's device current: the lookup is cheap, and
+// an address cached across calls would go stale if the device's primary context were reset.
+cudaError_t scratch_address(float** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<float*>(p);
   return cudaSuccess;
 }
 
@@ -58,7 +48,7 @@ extern "C" int spdhg_backproject_noalloc(spdhg_ctx* ctx, const float* y, float* 
     return SPDHG_ERR_STATE;
   }
   float* scratch = nullptr;
-  if (e == cudaSuccess) e = scratch_address(dev, &scratch);
+  if (e == cudaSuccess) e = scratch_address(&scratch);
   if (e != cudaSuccess) {
     ctx->err = std::string("spdhg_backproject_noalloc: ") + cudaGetErrorString(e);
     return SPDHG_ERR_CUDA;

@@ -220,4 +220,34 @@ cudaError_t launch_side_max_grad(const DevGeom& g, const float* side, double* pa
   return cudaGetLastError();
 }
 
+// PSNR terms (Sec. 4): out[0] = sum_j (x_j - xs_j)^2, out[1] = max_j |xs_j|, both in FP64
+__global__ void k_psnr_terms(const float* __restrict__ x, const float* __restrict__ xs, int64_t n,
+                             double* partial_sq, double* partial_max) {
+  __shared__ double sh[256];
+  double acc = 0.0, mx = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    const double d = (double)x[j] - (double)xs[j];
+    acc += d * d;
+    mx = fmax(mx, fabs((double)xs[j]));
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial_sq[blockIdx.x] = s;
+  __syncthreads();
+  sh[threadIdx.x] = mx;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+    if (threadIdx.x < k) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + k]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial_max[blockIdx.x] = sh[0];
+}
+
+cudaError_t launch_psnr_terms(const float* x, const float* xs, int64_t n, double* partial, int nblocks,
+                              double* out, cudaStream_t s) {
+  k_psnr_terms<<<nblocks, 256, 0, s>>>(x, xs, n, partial, partial + nblocks);
+  k_finish_sum<<<1, 256, 0, s>>>(partial, nblocks, out);
+  k_finish_max<<<1, 256, 0, s>>>(partial + nblocks, nblocks, out + 1);
+  return cudaGetLastError();
+}
+
 }  // namespace spdhg

@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(1024) k_prior(DevGeom g, PriorArgs a, int cols
       const float* sq = st + 2 * xv_sz;
       const float zn = sq[3 * cell_sz + me] + dz;
       a.z[idx] = zn;
-      a.x_out[idx] = fmaxf(xc - sq[4 * cell_sz + me] * fmaf(dz, a.inv_p, zn), 0.f);
+      a.x_out[idx] = prox_nonneg(xc - sq[4 * cell_sz + me] * fmaf(dz, a.inv_p, zn));
     }
     by_prev = b[1];
     __syncthreads();  // stage iy % S is refilled by the next iteration's copy
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256) k_tgv0_primal(DevGeom g, TgvArgs a) {
     }
     const float zn = a.zu[idx] + dz;
     a.zu[idx] = zn;
-    a.u_out[idx] = fmaxf(a.u_in[idx] - a.Tu[idx] * fmaf(dz, a.inv_p, zn), 0.f);
+    a.u_out[idx] = prox_nonneg(a.u_in[idx] - a.Tu[idx] * fmaf(dz, a.inv_p, zn));
   }
 }
 
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256) k_tgv1_primal(DevGeom g, TgvArgs a) {
       a.zw[k * N + idx] = zwn;
       a.w_out[k * N + idx] = a.w_in[k * N + idx] - a.Tw * fmaf(dzw[k], a.inv_p, zwn);
     }
-    a.u_out[idx] = fmaxf(a.u_in[idx] - a.Tu[idx] * a.zu[idx], 0.f);
+    a.u_out[idx] = prox_nonneg(a.u_in[idx] - a.Tu[idx] * a.zu[idx]);
   }
 }
 

@@ -13,6 +13,9 @@
 // transpose of the projector (up to the order of the sums).  No float atomics are used: the
 // forward kernel owns one LOR line per block, the backward kernel one voxel column per thread
 // group.
+#include <algorithm>
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace spdhg {
@@ -196,7 +199,8 @@ __device__ __forceinline__ int row_entries(const DevGeom& g, const Line& L, bool
   return n;
 }
 
-constexpr int kFwdChunk = 32;  // pixel entries per double-buffered chunk
+constexpr int kFwdChunk = 16;  // pixel entries per double-buffered chunk
+constexpr int kRunsPerWarp = 2;  // 32-plane runs per warp (lane = plane within a run)
 
 // Block-wide exclusive prefix sum of one int per thread (blockDim <= 1024); returns the
 // exclusive prefix and writes the total to *total.  Uses `scratch` (>= 33 ints of shared).
@@ -227,66 +231,101 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* scratch, int* to
   return excl;
 }
 
-// Forward projection.  A block owns the rows [row_lo, row_hi) of one transaxial LOR line
-// (view, radial bin) and all its planes.  All threads first find the pixels the line crosses in
-// those rows (exact intervals, compacted); the entries are then processed in chunks of
-// kFwdChunk: the x columns of chunk c+1 are copied to shared memory (cp.async, with NT-1 zeros
-// on each side so that taps leaving the image read zeros) and its axial taps computed while
-// chunk c is accumulated, one thread per plane.  When several blocks share a line, each writes
-// partial plane sums and the last one to finish reduces them in a fixed order.
-template <int NT, int PPT, int MODE>
-__global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap, int split, int xs_stride,
-                                                 FwdArgs a, float* part_acc, float* part_chord,
-                                                 unsigned* tickets) {
+// Axial taps of one (pixel entry, segment) pair as the gather reads them: lengths of taps
+// 0..NT-1 and, in `off`, the offset of plane 0's tap 0 in the staged x column (low 28 bits) and
+// the entry's own tap count (top bits; lengths past it are zero).
+struct TapRec {
+  float l0, l1, l2;
+  int off;
+};
+struct TapRec4 {  // geometries whose LORs cross four slices inside a pixel
+  float l0, l1, l2;
+  int off;
+  float l3, pad0, pad1, pad2;
+};
+template <int NT>
+using TapRecT = typename std::conditional<(NT > 3), TapRec4, TapRec>::type;
+constexpr int kOffBits = 28;
+constexpr int kOffMask = (1 << kOffBits) - 1;
+
+__device__ __forceinline__ float2 ffma2_bcast(float l, float xa, float xb, float2 acc) {
+  return __ffma2_rn(make_float2(l, l), make_float2(xa, xb), acc);
+}
+
+// sum_t L_t x[-t] over the entry's taps (scalar; one plane)
+template <int NT, class Rec>
+__device__ __forceinline__ float taps_dot(const Rec& t, int nt, const float* xp, float acc) {
+  acc = fmaf(t.l0, xp[0], acc);
+  if (NT > 1 && nt > 1) {
+    acc = fmaf(t.l1, xp[-1], acc);
+    if (NT > 2 && nt > 2) {
+      acc = fmaf(t.l2, xp[-2], acc);
+      if constexpr (NT > 3) {
+        if (nt > 3) acc = fmaf(t.l3, xp[-3], acc);
+      }
+    }
+  }
+  return acc;
+}
+
+// Forward projection.  Block (line, row part, plane part) owns the rows [row_lo, row_hi) of one
+// transaxial LOR line (view, radial bin) and a contiguous range of the line's plane runs (32
+// consecutive planes of one segment, segment-major); warp w owns two neighbouring runs and lane l
+// plane q0 + l of each.  All threads first find the pixels the line crosses in those rows (exact
+// intervals, compacted); the entries are then processed in chunks of kFwdChunk: the x columns of
+// chunk c+1 are copied to shared memory (cp.async) inside zero frames wide enough for every tap
+// of every plane of the segments (the axial bound of the geometry, so no plane needs a range
+// test), and its axial taps computed while chunk c is accumulated.  When both runs of a warp lie
+// in one segment, one tap record serves both and a packed FP32 FMA accumulates the two planes.
+// When several row parts share a line, each writes partial plane sums and the last one to finish
+// reduces them in a fixed order.
+template <int NT, int MODE>
+__global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap, int rsplit, int xs_stride,
+                                                 int runs_per_part, int nseg_tab, FwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int scan_scratch[33];
-  constexpr int PAD = NT - 1;
-  float* xs = reinterpret_cast<float*>(smem);                             // [2][kFwdChunk][xs_stride]
-  float4* tapL = reinterpret_cast<float4*>(xs + 2 * kFwdChunk * xs_stride);  // [2][n_seg][kFwdChunk]
-  int4* tapM = reinterpret_cast<int4*>(tapL + 2 * g.n_seg * kFwdChunk);      // [2][n_seg][kFwdChunk]
-  Entry* ent = reinterpret_cast<Entry*>(tapM + 2 * g.n_seg * kFwdChunk);     // [ecap]
+  const int FL = g.fz_lo;
+  float* xs = reinterpret_cast<float*>(smem);                                  // [2][kFwdChunk][xs_stride]
+  using Rec = TapRecT<NT>;
+  Rec* taps = reinterpret_cast<Rec*>(xs + 2 * kFwdChunk * xs_stride);          // [2][nseg_tab][kFwdChunk]
+  Entry* ent = reinterpret_cast<Entry*>(taps + 2 * nseg_tab * kFwdChunk);      // [ecap]
   const int nz = g.nz;
 
-  const int line = blockIdx.x / split, part = blockIdx.x - line * split;
-  const int l = line / g.R, r = line - (line / g.R) * g.R;
+  const int line = blockIdx.x, rpart = blockIdx.y, ppart = blockIdx.z;
+  const int l = line / g.R, r = line - l * g.R;
   const int v = subset_view(g, subset, l);
   const Line L = make_line(g, v, r);
 
-  // planes of this thread: lane of warp-sized runs of one segment (run = PPT * warp + k, so the
-  // runs of a warp are neighbours in the run table and usually share their segment)
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  int pseg[PPT], pq[PPT], pp[PPT];
-  bool pvalid[PPT];
-  float acc[PPT], chord[PPT];
+  // this thread's planes: lane of runs rf + 2w and rf + 2w + 1 of the plane part
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int rfirst = ppart * runs_per_part;
+  const int rlast = min(g.n_runs, rfirst + runs_per_part) - 1;
+  const int g_lo = g.runs[rfirst].x, g_hi = g.runs[rlast].x;
+  int gs_[kRunsPerWarp], qv_[kRunsPerWarp], qr_[kRunsPerWarp];
+  bool valid_[kRunsPerWarp];
 #pragma unroll
-  for (int k = 0; k < PPT; ++k) {
-    const int run = wi * PPT + k;
-    acc[k] = 0.f;
-    chord[k] = 0.f;
-    pseg[k] = -1;
-    pq[k] = 0;
-    pp[k] = 0;
-    pvalid[k] = false;
-    if (run < g.n_runs) {
-      const int2 ru = g.runs[run];
-      const SegDev sd = g.seg[ru.x];
-      pseg[k] = ru.x;
-      pq[k] = ru.y + lane;
-      pp[k] = sd.p0 + pq[k];
-      pvalid[k] = pq[k] < sd.n;
-    }
+  for (int k = 0; k < kRunsPerWarp; ++k) {
+    const int run = rfirst + kRunsPerWarp * wi + k;
+    const int2 ru = g.runs[min(run, rlast)];
+    const SegDev sd = g.seg[ru.x];
+    gs_[k] = ru.x;
+    qv_[k] = ru.y + lane;                        // the plane of this lane
+    valid_[k] = run <= rlast && qv_[k] < sd.n;
+    qr_[k] = min(qv_[k], sd.n - 1);              // the plane read (inside the segment's frames)
   }
-  // zero pads of the staged columns (never overwritten by the copies)
-  if constexpr (PAD > 0) {
-    for (int i = threadIdx.x; i < 2 * kFwdChunk * 2 * PAD; i += blockDim.x) {
-      const int col = i / (2 * PAD), k = i - col * (2 * PAD);
-      xs[col * xs_stride + (k < PAD ? k : nz + k)] = 0.f;
-    }
+  const bool same = gs_[0] == gs_[1];            // warp-uniform
+
+  // zero frames of the staged columns (never overwritten); SIGMA stages ones: the projection of
+  // the constant image is the chord of each LOR inside the image
+  for (int i = threadIdx.x; i < 2 * kFwdChunk * xs_stride; i += blockDim.x) {
+    const int k = i % xs_stride;
+    if (MODE == FWD_SIGMA) xs[i] = (k >= FL && k < FL + nz) ? 1.f : 0.f;
+    else if (k < FL || k >= FL + nz) xs[i] = 0.f;
   }
   const bool ydom = fabsf(L.c_hi) >= fabsf(L.s_hi);  // |dy| >= |dx|: walk the rows of y
   const int nrows_all = ydom ? g.ny : g.nx;
-  const int rows_per_part = (nrows_all + split - 1) / split;
-  const int row_lo = part * rows_per_part, row_hi = min(nrows_all, row_lo + rows_per_part);
+  const int rows_per_part = (nrows_all + rsplit - 1) / rsplit;
+  const int row_lo = rpart * rows_per_part, row_hi = min(nrows_all, row_lo + rows_per_part);
 
   // A. this block's rows -> exact pixel intervals, compacted into ent[]
   int n_ent = 0;
@@ -302,33 +341,41 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
   }
   __syncthreads();
 
+  const int nsb = g_hi - g_lo + 1;
   auto stage = [&](int c) {  // x columns + taps of chunk c into buffer c & 1
     const int buf = c & 1;
     const int e0 = c * kFwdChunk, ne = min(kFwdChunk, n_ent - e0);
     float* xb = xs + buf * kFwdChunk * xs_stride;
-    // one warp per entry, lanes along z: no division or entry lookup per staged value
-    const int nw = blockDim.x >> 5;
-    for (int e = wi; e < ne; e += nw) {
-      const float* src = a.x + (size_t)ent[e0 + e].col * nz;
-      float* dst = xb + e * xs_stride + PAD;
-      for (int iz = lane; iz < nz; iz += 32) cp_async4(dst + iz, src + iz);
+    if (MODE != FWD_SIGMA) {
+      // one warp per entry, lanes along z
+      for (int e = wi; e < ne; e += nw) {
+        const float* src = a.x + (size_t)ent[e0 + e].col * nz;
+        float* dst = xb + e * xs_stride + FL;
+        for (int iz = lane; iz < nz; iz += 32) cp_async4(dst + iz, src + iz);
+      }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
-    float4* tl = tapL + buf * g.n_seg * kFwdChunk;
-    int4* tm = tapM + buf * g.n_seg * kFwdChunk;
-    for (int it = threadIdx.x; it < g.n_seg * ne; it += blockDim.x) {
+    Rec* tb = taps + buf * nseg_tab * kFwdChunk;
+    for (int it = threadIdx.x; it < nsb * ne; it += blockDim.x) {
       const int gs = it / ne, e = it - gs * ne;
       float Lk[4] = {0.f, 0.f, 0.f, 0.f};
-      const int j0 = segment_taps<NT>(g, r, gs, ent[e0 + e].I, Lk);
+      int j0 = segment_taps<NT>(g, r, g_lo + gs, ent[e0 + e].I, Lk);
+      // the geometry's axial bound keeps every read inside the framed column; the clamp only
+      // guards shared memory should a rounding case fall outside it
+      const SegDev sd = g.seg[g_lo + gs];
+      j0 = min(max(j0, sd.jlo), sd.jhi);
       int nt = NT;
       while (nt > 1 && Lk[nt - 1] == 0.f) --nt;
-      const int slot = gs * kFwdChunk + e;
-      tl[slot] = make_float4(Lk[0], Lk[1], Lk[2], Lk[3]);
-      // plane q, tap t reads xs[e * stride + PAD + q - j0 - t]; useful while 0 <= q - j0 < nz + PAD
-      tm[slot] = make_int4(e * xs_stride + PAD - j0, j0, nt, 0);
+      Rec& rec = tb[gs * kFwdChunk + e];
+      rec.l0 = Lk[0];
+      rec.l1 = NT > 1 ? Lk[1] : 0.f;
+      rec.l2 = NT > 2 ? Lk[2] : 0.f;
+      rec.off = (e * xs_stride + FL - j0) | (nt << kOffBits);
+      if constexpr (NT > 3) rec.l3 = Lk[3];
     }
   };
 
+  float acc[kRunsPerWarp] = {0.f, 0.f};
   const int nchunks = (n_ent + kFwdChunk - 1) / kFwdChunk;
   if (nchunks > 0) stage(0);
   for (int c = 0; c < nchunks; ++c) {
@@ -342,129 +389,87 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
     const int buf = c & 1;
     const int ne = min(kFwdChunk, n_ent - c * kFwdChunk);
     const float* xb = xs + buf * kFwdChunk * xs_stride;
-    const float4* tl = tapL + buf * g.n_seg * kFwdChunk;
-    const int4* tm = tapM + buf * g.n_seg * kFwdChunk;
-    // all runs of this warp in one segment (warp-uniform): one load of each entry's taps serves them
-    bool same = pseg[0] >= 0;
-#pragma unroll
-    for (int k = 1; k < PPT; ++k) same = same && (pseg[k] < 0 || pseg[k] == pseg[0]);
-    if (MODE != FWD_SIGMA && PPT > 1 && same) {
-      const float4* tlk = tl + pseg[0] * kFwdChunk;
-      const int4* tmk = tm + pseg[0] * kFwdChunk;
-      float sum[PPT];
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) sum[k] = 0.f;
+    const Rec* tr0 = taps + buf * nseg_tab * kFwdChunk + (gs_[0] - g_lo) * kFwdChunk;
+    if (same) {
+      float2 s2 = make_float2(0.f, 0.f);
+#pragma unroll 2
       for (int e = 0; e < ne; ++e) {
-        const int4 M = tmk[e];
-        const float4 Lv = tlk[e];
-        const float* xe = xb + M.x;
-        if (NT == 1 || M.z == 1) {  // tap count is uniform across the warp
-#pragma unroll
-          for (int k = 0; k < PPT; ++k)
-            if (pseg[k] >= 0 && (unsigned)(pq[k] - M.y) < (unsigned)(nz + PAD)) sum[k] = fmaf(Lv.x, xe[pq[k]], sum[k]);
-        } else if (NT == 2 || M.z == 2) {
-#pragma unroll
-          for (int k = 0; k < PPT; ++k)
-            if (pseg[k] >= 0 && (unsigned)(pq[k] - M.y) < (unsigned)(nz + PAD)) {
-              const float* xp = xe + pq[k];
-              sum[k] = fmaf(Lv.y, xp[-1], fmaf(Lv.x, xp[0], sum[k]));
+        const Rec t = tr0[e];
+        const int off = t.off & kOffMask, nt = NT > 1 ? (t.off >> kOffBits) : 1;
+        const float* xa = xb + off + qr_[0];
+        const float* xc = xb + off + qr_[1];
+        s2 = ffma2_bcast(t.l0, xa[0], xc[0], s2);
+        if (NT > 1 && nt > 1) {
+          s2 = ffma2_bcast(t.l1, xa[-1], xc[-1], s2);
+          if (NT > 2 && nt > 2) {
+            s2 = ffma2_bcast(t.l2, xa[-2], xc[-2], s2);
+            if constexpr (NT > 3) {
+              if (nt > 3) s2 = ffma2_bcast(t.l3, xa[-3], xc[-3], s2);
             }
-        } else if (NT == 3 || M.z == 3) {
-#pragma unroll
-          for (int k = 0; k < PPT; ++k)
-            if (pseg[k] >= 0 && (unsigned)(pq[k] - M.y) < (unsigned)(nz + PAD)) {
-              const float* xp = xe + pq[k];
-              sum[k] = fmaf(Lv.z, xp[-2], fmaf(Lv.y, xp[-1], fmaf(Lv.x, xp[0], sum[k])));
-            }
-        } else {
-#pragma unroll
-          for (int k = 0; k < PPT; ++k)
-            if (pseg[k] >= 0 && (unsigned)(pq[k] - M.y) < (unsigned)(nz + PAD)) {
-              const float* xp = xe + pq[k];
-              sum[k] = fmaf(Lv.w, xp[-3], fmaf(Lv.z, xp[-2], fmaf(Lv.y, xp[-1], fmaf(Lv.x, xp[0], sum[k]))));
-            }
+          }
         }
       }
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) acc[k] += sum[k];
-    }
-#pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      if (MODE != FWD_SIGMA && PPT > 1 && same) break;  // done above
-      if (pseg[k] < 0) break;  // warp-uniform: no more runs for this warp
-      const float4* tlk = tl + pseg[k] * kFwdChunk;
-      const int4* tmk = tm + pseg[k] * kFwdChunk;
-      const int q = pq[k];
-      float sum = 0.f;
+      acc[0] += s2.x;
+      acc[1] += s2.y;
+    } else {
+      const Rec* tr1 = taps + buf * nseg_tab * kFwdChunk + (gs_[1] - g_lo) * kFwdChunk;
+      float s0 = 0.f, s1 = 0.f;
       for (int e = 0; e < ne; ++e) {
-        const int4 M = tmk[e];     // warp broadcast: one segment per warp
-        const float4 Lv = tlk[e];
-        const int d = q - M.y;
-        const bool in = (unsigned)d < (unsigned)(nz + PAD);
-        const float* xp = xb + M.x + q;  // taps t read xp[-t], inside the zero-padded column
-        if (MODE == FWD_SIGMA) {  // chord of the LOR inside the image: taps whose slab exists
-          if (in)
-            chord[k] += (d < nz ? Lv.x : 0.f) + (NT > 1 && d >= 1 && d - 1 < nz ? Lv.y : 0.f) +
-                        (NT > 2 && d >= 2 && d - 2 < nz ? Lv.z : 0.f) + (NT > 3 && d >= 3 && d - 3 < nz ? Lv.w : 0.f);
-        } else if (NT == 1 || M.z == 1) {  // tap count is uniform across the warp
-          if (in) sum = fmaf(Lv.x, xp[0], sum);
-        } else if (NT == 2 || M.z == 2) {
-          if (in) sum = fmaf(Lv.y, xp[-1], fmaf(Lv.x, xp[0], sum));
-        } else if (NT == 3 || M.z == 3) {
-          if (in) sum = fmaf(Lv.z, xp[-2], fmaf(Lv.y, xp[-1], fmaf(Lv.x, xp[0], sum)));
-        } else {
-          if (in) sum = fmaf(Lv.w, xp[-3], fmaf(Lv.z, xp[-2], fmaf(Lv.y, xp[-1], fmaf(Lv.x, xp[0], sum))));
-        }
+        const Rec t0 = tr0[e], t1 = tr1[e];
+        s0 = taps_dot<NT>(t0, NT > 1 ? (t0.off >> kOffBits) : 1, xb + (t0.off & kOffMask) + qr_[0], s0);
+        s1 = taps_dot<NT>(t1, NT > 1 ? (t1.off >> kOffBits) : 1, xb + (t1.off & kOffMask) + qr_[1], s1);
       }
-      acc[k] += sum;
+      acc[0] += s0;
+      acc[1] += s1;
     }
     __syncthreads();
   }
 
-  if (split > 1) {
-    // publish this block's partial sums; the last block of the line reduces them
+  if (rsplit > 1) {
+    // publish this block's partial sums; the last row part of the (line, plane part) reduces them
     __shared__ unsigned last_sh;
-    const size_t pbase = ((size_t)line * split + part) * g.P;
+    const size_t pbase = ((size_t)line * rsplit + rpart) * g.P;
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      if (!pvalid[k]) continue;
-      const int p = pp[k];
-      part_acc[pbase + p] = acc[k];
-      if (MODE == FWD_SIGMA) part_chord[pbase + p] = chord[k];
-    }
+    for (int k = 0; k < kRunsPerWarp; ++k)
+      if (valid_[k]) a.part_acc[pbase + g.seg[gs_[k]].p0 + qv_[k]] = acc[k];
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last_sh = (atomicAdd(tickets + line, 1u) == (unsigned)split - 1u) ? 1u : 0u;
+    const size_t ticket = (size_t)line * gridDim.z + ppart;
+    if (threadIdx.x == 0) last_sh = (atomicAdd(a.tickets + ticket, 1u) == (unsigned)rsplit - 1u) ? 1u : 0u;
     __syncthreads();
     if (!last_sh) return;
     __threadfence();
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      if (!pvalid[k]) continue;
-      const int p = pp[k];
-      float sa = 0.f, sc = 0.f;
-      for (int q = 0; q < split; ++q) {  // fixed order: deterministic
-        const size_t o = ((size_t)line * split + q) * g.P + p;
-        sa += __ldcg(part_acc + o);
-        if (MODE == FWD_SIGMA) sc += __ldcg(part_chord + o);
-      }
+    for (int k = 0; k < kRunsPerWarp; ++k) {
+      if (!valid_[k]) continue;
+      float sa = 0.f;
+      for (int q = 0; q < rsplit; ++q)  // fixed order: deterministic
+        sa += __ldcg(a.part_acc + ((size_t)line * rsplit + q) * g.P + g.seg[gs_[k]].p0 + qv_[k]);
       acc[k] = sa;
-      chord[k] = sc;
     }
-    if (threadIdx.x == 0) tickets[line] = 0u;  // ready for the next launch
+    if (threadIdx.x == 0) a.tickets[ticket] = 0u;  // ready for the next launch
   }
 
 #pragma unroll
-  for (int k = 0; k < PPT; ++k) {
-    if (!pvalid[k]) continue;
-    const int p = pp[k];
+  for (int k = 0; k < kRunsPerWarp; ++k) {
+    if (!valid_[k]) continue;
+    const int p = g.seg[gs_[k]].p0 + qv_[k];
     const size_t j = ((size_t)v * g.R + r) * g.P + p;
+    const size_t jl = ((size_t)l * g.R + r) * g.P + p;  // subset-local index (= j for bin subsets)
+    if (!bin_in_subset(g, subset, j)) {  // a bin of another subset: not written; no dual change
+      if (MODE == FWD_DATA || MODE == FWD_EM) a.wdy[jl] = 0.f;
+      continue;
+    }
     const float mu = a.mult ? a.mult[j] : 1.f;
-    if (MODE == FWD_PROJECT) {
+    if (MODE == FWD_EM) {
+      // EM ratio backprojected by P^T = L^T diag(mult): mult_j b_j / ((P x)_j + r_j)  (Eq. EQU:OSEM)
+      const float bj = a.b[j];
+      a.wdy[jl] = bj > 0.f ? mu * bj / fmaf(mu, acc[k], a.r[j]) : 0.f;
+    } else if (MODE == FWD_PROJECT) {
       a.out[j] = mu * acc[k];
     } else if (MODE == FWD_SIGMA) {
       // sigma_j = gamma rho / (P_i 1)_j,  (P_i 1)_j = mult_j * chord_j  (Eq. EQU:STEPSIZE:PRECOND)
-      const float a1 = mu * chord[k];
+      const float a1 = mu * acc[k];
       a.out[j] = a1 > 0.f ? a.gamma_rho / a1 : 0.f;
     } else {
       // KL dual prox on this bin:  y+ = prox_{sigma varphi*}(y + sigma (P_i x)_j), evaluated as
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
       const float root = sqrtf(fmaf(wm, wm, 4.f * sb));
       const float yn = 2.f * (w - sb) / (w + 1.f + root);
       a.y[j] = yn;
-      a.wdy[((size_t)l * g.R + r) * g.P + p] = mu * (yn - yj);
+      a.wdy[jl] = mu * (yn - yj);
     }
   }
 }
@@ -670,11 +675,15 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
     } else if (MODE == BWD_SENS) {
       // T_i = rho p_i / (gamma (P_i^T 1)); +inf (kept) where the subset does not see the voxel
       if (acc[k] > 0.f) a.T[idx] = fminf(a.T[idx], a.sens_num / acc[k]);
+    } else if (MODE == BWD_EM) {
+      // u <- u / (P_i^T 1) * P_i^T (b_i / (P_i u + r_i)), 0 where the subset does not see the voxel
+      const float sens = a.T[idx];
+      a.x[idx] = sens > 0.f ? a.x[idx] * acc[k] / sens : 0.f;
     } else {
       // z = z + dz;  zbar = z + dz / p_i;  next primal step x = max(x - T zbar, 0)
       const float zn = a.z[idx] + acc[k];
       a.z[idx] = zn;
-      a.x[idx] = fmaxf(a.x[idx] - a.T[idx] * fmaf(acc[k], a.inv_p, zn), 0.f);
+      a.x[idx] = prox_nonneg(a.x[idx] - a.T[idx] * fmaf(acc[k], a.inv_p, zn));
     }
   }
 }
@@ -686,7 +695,8 @@ __global__ void k_gather_subset(DevGeom g, int subset, const float* __restrict__
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int l = (int)(i / per_view);
     const int64_t j = (int64_t)subset_view(g, subset, l) * per_view + (i - l * per_view);
-    w[i] = mult ? y[j] * mult[j] : y[j];
+    const float v = (y ? y[j] : 1.f) * (mult ? mult[j] : 1.f);
+    w[i] = bin_in_subset(g, subset, (size_t)j) ? v : 0.f;
   }
 }
 
@@ -697,59 +707,60 @@ __global__ void k_gather_subset(DevGeom g, int subset, const float* __restrict__
 int forward_split(const DevGeom& g, int subset) {
   if (g.tune[SPDHG_TUNE_FWD_SPLIT]) return g.tune[SPDHG_TUNE_FWD_SPLIT];
   // enough blocks for every SM: one LOR line per block is too few for small subsets
-  const int lines = subset_views(g, subset) * g.R;
+  const int lines = subset_views(g, subset) * g.R * forward_parts(g);
   const int nrows = g.nx > g.ny ? g.nx : g.ny;
   int split = 1;
   while (split < 8 && lines * split < 152 && nrows / (split * 2) >= 32) split *= 2;
   return split;
 }
 
-template <int NT, int PPT, int MODE>
-static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cudaStream_t s, int threads, int split) {
-  const int xs_stride = g.nz + 2 * (NT - 1);  // staged x column with zero pads
+// plane runs per block: two per warp, at most 16 warps
+static int forward_runs_per_part(const DevGeom& g) {
+  const int w = g.tune[SPDHG_TUNE_FWD_WARPS] ? g.tune[SPDHG_TUNE_FWD_WARPS] : 16;
+  return w * kRunsPerWarp;
+}
+
+int forward_parts(const DevGeom& g) {
+  const int rpp = forward_runs_per_part(g);
+  return (g.n_runs + rpp - 1) / rpp;
+}
+
+template <int NT, int MODE>
+static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cudaStream_t s) {
+  const int xs_stride = g.fz_stride;
   const int nrows = g.nx > g.ny ? g.nx : g.ny;
   const int ecap = 3 * nrows + 8;  // a line crosses at most two pixels per row of its dominant axis
+  const int rpp = forward_runs_per_part(g);
+  const int parts = (g.n_runs + rpp - 1) / rpp;
+  const int threads = 32 * ((std::min(rpp, g.n_runs) + kRunsPerWarp - 1) / kRunsPerWarp);
+  const int nseg_tab = g.n_seg;  // a block computes the taps of the segments its runs span
   const size_t smem = (size_t)2 * kFwdChunk * xs_stride * sizeof(float) +
-                      (size_t)2 * g.n_seg * kFwdChunk * (sizeof(float4) + sizeof(int4)) + (size_t)ecap * sizeof(Entry);
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+                      (size_t)2 * nseg_tab * kFwdChunk * sizeof(TapRecT<NT>) + (size_t)ecap * sizeof(Entry);
+  if (smem > 200 * 1024 || (size_t)kFwdChunk * xs_stride >= ((size_t)1 << kOffBits)) return cudaErrorInvalidValue;
   if (MODE == FWD_DATA && !a.sigma) return cudaErrorInvalidValue;
+  if ((MODE == FWD_DATA || MODE == FWD_EM) && (!a.b || !a.r || !a.wdy)) return cudaErrorInvalidValue;
   {
-    cudaError_t e = allow_dynamic_smem(k_forward<NT, PPT, MODE>, smem);
+    cudaError_t e = allow_dynamic_smem(k_forward<NT, MODE>, smem);
     if (e != cudaSuccess) return e;
   }
   const int lines = subset_views(g, subset) * g.R;
   if (lines == 0) return cudaSuccess;
-  if (split > 1 && (!a.part_acc || !a.part_chord || !a.tickets || (size_t)lines * split * g.P > a.part_cap ||
-                    (size_t)lines > a.ticket_cap))
+  const int rsplit = forward_split(g, subset);
+  if (rsplit > 1 && (!a.part_acc || !a.tickets || (size_t)lines * rsplit * g.P > a.part_cap ||
+                     (size_t)lines * parts > a.ticket_cap))
     return cudaErrorInvalidValue;
-  k_forward<NT, PPT, MODE><<<lines * split, threads, smem, s>>>(g, subset, ecap, split, xs_stride, a, a.part_acc,
-                                                                a.part_chord, a.tickets);
+  dim3 grid(lines, rsplit, parts);
+  k_forward<NT, MODE><<<grid, threads, smem, s>>>(g, subset, ecap, rsplit, xs_stride, rpp, nseg_tab, a);
   return cudaGetLastError();
-}
-
-template <int NT, int MODE>
-static cudaError_t fwd_ppt(const DevGeom& g, int subset, const FwdArgs& a, cudaStream_t s) {
-  const int split = forward_split(g, subset);
-  const int nwarps = g.tune[SPDHG_TUNE_FWD_WARPS] ? g.tune[SPDHG_TUNE_FWD_WARPS]
-                                                  : (g.n_runs < 16 ? (g.n_runs < 4 ? 4 : g.n_runs) : 16);
-  const int ppt = (g.n_runs + nwarps - 1) / nwarps;                      // runs per warp
-  const int threads = nwarps * 32;
-  switch (ppt) {
-    case 1: return fwd_launch<NT, 1, MODE>(g, subset, a, s, threads, split);
-    case 2: return fwd_launch<NT, 2, MODE>(g, subset, a, s, threads, split);
-    case 3: return fwd_launch<NT, 3, MODE>(g, subset, a, s, threads, split);
-    case 4: return fwd_launch<NT, 4, MODE>(g, subset, a, s, threads, split);
-    default: return cudaErrorInvalidValue;
-  }
 }
 
 template <int MODE>
 static cudaError_t fwd_nt(const DevGeom& g, int subset, const FwdArgs& a, cudaStream_t s) {
   switch (g.taps) {
-    case 1: return fwd_ppt<1, MODE>(g, subset, a, s);
-    case 2: return fwd_ppt<2, MODE>(g, subset, a, s);
-    case 3: return fwd_ppt<3, MODE>(g, subset, a, s);
-    case 4: return fwd_ppt<4, MODE>(g, subset, a, s);
+    case 1: return fwd_launch<1, MODE>(g, subset, a, s);
+    case 2: return fwd_launch<2, MODE>(g, subset, a, s);
+    case 3: return fwd_launch<3, MODE>(g, subset, a, s);
+    case 4: return fwd_launch<4, MODE>(g, subset, a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -759,6 +770,7 @@ cudaError_t launch_forward(const DevGeom& g, int subset, int mode, const FwdArgs
     case FWD_PROJECT: return fwd_nt<FWD_PROJECT>(g, subset, a, s);
     case FWD_SIGMA: return fwd_nt<FWD_SIGMA>(g, subset, a, s);
     case FWD_DATA: return fwd_nt<FWD_DATA>(g, subset, a, s);
+    case FWD_EM: return fwd_nt<FWD_EM>(g, subset, a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -819,6 +831,7 @@ cudaError_t launch_backward(const DevGeom& g, int subset, int mode, const BwdArg
     case BWD_OUT: return bwd_nt<BWD_OUT>(g, subset, a, s);
     case BWD_SENS: return bwd_nt<BWD_SENS>(g, subset, a, s);
     case BWD_UPDATE: return bwd_nt<BWD_UPDATE>(g, subset, a, s);
+    case BWD_EM: return bwd_nt<BWD_EM>(g, subset, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

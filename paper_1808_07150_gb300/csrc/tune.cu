@@ -119,8 +119,8 @@ extern "C" int spdhg_autotune(spdhg_ctx* ctx, int reps, int* chosen, void* strea
   std::vector<Knob> knobs;
   {
     Knob k{SPDHG_TUNE_FWD_WARPS, true, {}};
-    for (int w : {4, 8, 16})
-      if ((g.n_runs + w - 1) / w <= 4) k.values.push_back(w);
+    for (int w : {2, 4, 8, 16})
+      if (w == 2 || (g.n_runs + 1) / 2 > w / 2) k.values.push_back(w);
     knobs.push_back(k);
   }
   {

@@ -21,6 +21,14 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / (nb if nb > 0 else 1.0))
 
 
+def maxerr(a, b):
+    """Elementwise bound: max |a - b| / max |b| (a few wrong entries cannot hide in the norm)."""
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    mb = float(np.abs(b).max()) if b.size else 0.0
+    return float(np.abs(a - b).max() / (mb if mb > 0 else 1.0)) if a.size else 0.0
+
+
 def wide_2d(n_subsets=3):
     """Tiny 2-D geometry whose outer radial bins miss the image (A_i 1 = 0 there)."""
     return synth.Scanner(nx=8, ny=8, nz=1, vx=1.0, vy=1.0, vz=1.0, n_radial=15, d_radial=1.0,

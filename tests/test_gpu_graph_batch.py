@@ -32,11 +32,12 @@ def _params(pkg, kind, epochs, graph, seed=1808, every=1):
 
 
 def _oracle_run(sc, prob, kind, epochs, seed, x0):
-    import paper_1808_07150_gb300 as pkg
     prior = _prior(kind)
     probs = O.probabilities(sc.n_subsets, prior)
     ipe = O.iters_per_epoch(sc.n_subsets, probs)
-    seq = np.concatenate([pkg.spdhg_sample(seed, e * ipe, ipe, probs) for e in range(epochs)])
+    # the oracle's own sampler (pinned bit-equal to the library's elsewhere): nothing of the
+    # oracle's input comes from the product
+    seq = np.concatenate([O.sample(seed, ipe, probs, offset=e * ipe) for e in range(epochs)])
     st, steps = O.spdhg(prob, prior, seq, probs, x0=x0.reshape(sc.image_shape).astype(np.float64))
     return O.next_primal(st, steps)
 
@@ -164,7 +165,7 @@ def test_autotune_keeps_state_and_parity(kind):
         after = state()
         for k in keys:
             np.testing.assert_array_equal(after[k], before[k], err_msg=k)
-        assert chosen["fwd_warps"] in (0, 4, 8, 16)
+        assert chosen["fwd_warps"] in (0, 2, 4, 8, 16)
         assert chosen["fwd_split"] in (0, 1, 2, 4, 8)
         if kind == "dtv":
             assert 2 <= chosen["prior_cols"] <= 32 and chosen["prior_ychunk"] in (16, 32, 64, 128, 256)

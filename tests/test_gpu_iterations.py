@@ -157,6 +157,26 @@ def test_invalid_inputs_are_rejected():
             ctx.spdhg_project(torch.zeros(sc.n_voxels, device="cuda"), torch.zeros(sc.n_bins, device="cuda"), sc.n_subsets)
 
 
+def test_non_finite_objective_is_reported_as_diverged():
+    """A start image holding +Inf makes the FP64 objective non-finite after the first epoch:
+    spdhg_run stops there with SPDHG_ERR_DIVERGED (the failure is made on the host; no kernel
+    faults, the arithmetic just carries Inf / NaN)."""
+    import paper_1808_07150_gb300 as pkg
+    sc = synth.tiny_2d()
+    d, _ = problem(sc)
+    x = np.full(sc.image_shape, np.inf, np.float32)
+    with pkg.Context(sc) as ctx:
+        upload(ctx, d)
+        with pytest.raises(pkg.SpdhgError) as e:
+            ctx.spdhg_run(pkg.make_params("tv", alpha=0.1, epochs=3, objective_every=1), x)
+        assert e.value.code == pkg._capi.ERR_DIVERGED
+        assert b"not finite" in pkg._capi.lib().spdhg_last_error(ctx.h)
+        # the context stays usable: a finite start runs to the end
+        x0 = np.zeros(sc.image_shape, np.float32)
+        rep = ctx.spdhg_run(pkg.make_params("tv", alpha=0.1, epochs=2, objective_every=1), x0)
+        assert rep["epochs_done"] == 2 and np.all(np.isfinite(rep["objective"]))
+
+
 @pytest.mark.parametrize("sc", [synth.tiny_3d(steep=True), synth.config_2d()], ids=lambda s: s.name)
 def test_scalar_step_sizes_and_iterations_match_oracle(sc):
     """precond = 0 (Eq. EQU:STEPSIZE:SCALAR): sigma_i = gamma rho / ||P_i|| on the bins of subset i,

@@ -4,7 +4,7 @@ per-bin multipliers, dTV with a side image.
 
 Both iterations start from the setup state (x = max(x0, 0), y = 0, z = 0, q = 0).  Compared:
 the dual y of the subset's 287,928 bins and the prior dual q and dz on all voxels (relative L2
-<= 1e-5), and z, x at sampled voxels where the oracle evaluates T by its definition
+<= 1e-5, and elementwise max |gpu - ref| / max |ref| <= 1e-5), and z, x at sampled voxels where the oracle evaluates T by its definition
 (min over the 252 subsets of rho p_i / (P_i^T 1), and the prior's scalar step).
 """
 import numpy as np
@@ -14,7 +14,7 @@ import synth
 from oracle import _native
 from oracle import algorithms as O
 
-from gpu_helpers import dev, host, rel
+from gpu_helpers import dev, host, maxerr, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -66,6 +66,7 @@ def test_mmr_step_sizes_at_sampled_voxels(mmr):
     sc, d, x0, vox, T, probs, prior = mmr
     g = _run(sc, d, x0, [], ["T"])
     assert rel(g["T"][vox], T) < 1e-5
+    assert maxerr(g["T"][vox], T) < 1e-5
 
 
 def test_mmr_data_iteration(mmr):
@@ -79,12 +80,15 @@ def test_mmr_data_iteration(mmr):
     sigma = np.where(a1 > 0, 0.99 / np.where(a1 > 0, a1, 1.0), 0.0)
     y_new = O.kl_prox(sigma * ax, sigma, d["b"].astype(np.float64)[mask], d["r"].astype(np.float64)[mask])
     assert rel(g["y"].reshape(sc.sino_shape)[mask], y_new) < 1e-5
+    assert maxerr(g["y"].reshape(sc.sino_shape)[mask], y_new) < 1e-5
     dy = np.zeros(sc.sino_shape)
     dy[mask] = y_new
     dz = _native.adjoint_at_voxels(sc, dy * mult, vox, SUBSET)
     assert rel(g["z"][vox], dz) < 1e-5
+    assert maxerr(g["z"][vox], dz) < 1e-5
     x_ref = np.maximum(xd.ravel()[vox] - T * (dz + dz / probs[SUBSET]), 0.0)
     assert rel(g["x"][vox], x_ref) < 1e-5
+    assert maxerr(g["x"][vox], x_ref) < 1e-5
 
 
 def test_mmr_dtv_prior_iteration(mmr):
@@ -97,6 +101,9 @@ def test_mmr_dtv_prior_iteration(mmr):
     q_new = O.proj_l2(sig * O.dtv_apply(xi, O.grad(xd), prior.gamma_d), ALPHA)
     dz = O.grad_adj(O.dtv_apply(xi, q_new, prior.gamma_d))
     assert rel(g["q"], q_new) < 1e-5
+    assert maxerr(g["q"], q_new) < 1e-5
     assert rel(g["z"], dz) < 1e-5
+    assert maxerr(g["z"], dz) < 1e-5
     x_ref = np.maximum(xd.ravel()[vox] - T * (dz.ravel()[vox] * (1 + 1 / probs[m])), 0.0)
     assert rel(g["x"][vox], x_ref) < 1e-5
+    assert maxerr(g["x"][vox], x_ref) < 1e-5

@@ -1,7 +1,8 @@
 """GPU parity of the projector, backprojector and step sizes against the FP64 oracle.
 
 Tolerance: per-operator relative L2 error <= 1e-5 in FP32 (the stated bar for single
-operators).  The GPU adjoint pairing <P x, y> vs <x, P^T y> is held to 2e-6: both directions
+operators), and elementwise max |gpu - ref| / max |ref| <= 1e-5 so that a few wrong bins or voxels
+cannot hide under the norm.  The GPU adjoint pairing <P x, y> vs <x, P^T y> is held to 2e-6: both directions
 use bit-identical lengths, so only the summation order differs.
 """
 import numpy as np
@@ -11,7 +12,7 @@ import synth
 from oracle import _native
 from oracle import algorithms as O
 
-from gpu_helpers import dev, host, problem, rel, upload, wide_2d
+from gpu_helpers import dev, host, maxerr, problem, rel, upload, wide_2d
 
 pytestmark = pytest.mark.gpu
 
@@ -45,10 +46,12 @@ def test_project_and_backproject_match_oracle(sc):
             mask = O.subset_mask(sc, subset)
             y_ref = O.project(sc, x.astype(np.float64), subset, mult.astype(np.float64))
             assert rel(host(y_gpu)[mask.ravel()], y_ref[mask]) < 1e-5
+            assert maxerr(host(y_gpu)[mask.ravel()], y_ref[mask]) < 1e-5
             if subset >= 0:  # bins of other subsets are not written
                 assert np.all(host(y_gpu)[~mask.ravel()] == 0.0)
             bp_ref = O.backproject(sc, yv.astype(np.float64) * mask, subset, mult.astype(np.float64))
             assert rel(host(bp_gpu), bp_ref) < 1e-5
+            assert maxerr(host(bp_gpu), bp_ref) < 1e-5
             # adjoint pairing on the GPU results
             lhs = float(np.dot(host(y_gpu)[mask.ravel()], yv.astype(np.float64).ravel()[mask.ravel()]))
             rhs = float(np.dot(x.astype(np.float64).ravel(), host(bp_gpu)))
@@ -73,8 +76,10 @@ def test_sigma_and_T_match_oracle(sc):
         ctx.spdhg_get("T", T)
         torch.cuda.synchronize()
     assert rel(host(sig), st["sigma"]) < 1e-5
+    assert maxerr(host(sig), st["sigma"]) < 1e-5
     assert np.array_equal(host(sig) == 0, st["sigma"].ravel() == 0)
     assert rel(host(T), st["T"]) < 1e-5
+    assert maxerr(host(T), st["T"]) < 1e-5
 
 
 def test_mmr_scale_operators_on_sampled_outputs():
@@ -95,6 +100,7 @@ def test_mmr_scale_operators_on_sampled_outputs():
                              for r, p in zip(rng.integers(0, sc.n_radial, 1500), rng.integers(0, sc.n_planes, 1500))])
             ref = _native.line_integrals_at(sc, x.astype(np.float64), bins) * mult.ravel()[bins]
             assert rel(host(y_gpu)[bins], ref) < 1e-5
+            assert maxerr(host(y_gpu)[bins], ref) < 1e-5
             yv = np.zeros(sc.sino_shape, np.float32)
             yv[subset] = rng.standard_normal(yv[subset].shape).astype(np.float32)
             bp = torch.zeros(sc.n_voxels, device="cuda")
@@ -103,3 +109,4 @@ def test_mmr_scale_operators_on_sampled_outputs():
             vox = rng.integers(0, sc.n_voxels, 96)
             ref_bp = _native.adjoint_at_voxels(sc, yv.astype(np.float64) * mult, vox, subset)
             assert rel(host(bp)[vox], ref_bp) < 1e-5
+            assert maxerr(host(bp)[vox], ref_bp) < 1e-5

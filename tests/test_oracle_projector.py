@@ -1,7 +1,7 @@
 """Pins of the oracle's projector against what geometry fixes independently of it.
 
 The projector's definition (exact line integral of the piecewise-constant image along the
-LOR segment, Sec. 1.2 "P performs the projection") is checked against: an independent dense
+LOR segment, the projection model of Sec. 1.2) is checked against: an independent dense
 matrix by per-voxel slab clipping, exact lengths through axis-aligned boxes of voxels (a
 numpy slab clip of one box, no per-voxel code), analytic disk chords, and the adjoint identity.
 """

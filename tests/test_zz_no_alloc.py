@@ -12,7 +12,7 @@ import pytest
 
 import synth
 
-from gpu_helpers import dev, host, rel
+from gpu_helpers import dev, host
 
 pytestmark = pytest.mark.gpu
 
@@ -39,7 +39,8 @@ def test_noalloc_backprojection_matches_backproject_twice(sc):
             ctx.spdhg_backproject(y, ref, subset)
             assert _call_noalloc(ctx, y, got, subset) == 0, pkg._capi.lib().spdhg_last_error(ctx.h)
             torch.cuda.synchronize()
-            assert rel(host(got), host(ref)) <= 1e-6
+            # the same gather and backprojection kernels on the same inputs: identical bits
+            np.testing.assert_array_equal(host(got), host(ref))
 
 
 def test_noalloc_rejects_subsets_beyond_its_scratch():
