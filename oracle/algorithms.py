@@ -42,12 +42,43 @@ def subset_mask(sc, i):
     return m
 
 
+def _line_integrals(sc, x, subset):
+    """L x on the view subset (subset < 0: all views).  A mashed bin is the sum of the line
+    integrals of its LOR components (exact mashing): each component family is projected as a
+    scanner of its own and added into the planes it belongs to."""
+    comps = synth_components(sc)
+    if comps is None:
+        return _native.line_integrals(sc, x, subset)
+    y = np.zeros(sc.sino_shape)
+    for vs, planes in comps:
+        y[:, :, planes] += _native.line_integrals(vs, x, subset)
+    return y
+
+
+def _line_integrals_adjoint(sc, y, subset):
+    comps = synth_components(sc)
+    if comps is None:
+        return _native.line_integrals_adjoint(sc, y, subset)
+    out = np.zeros(sc.image_shape)
+    for vs, planes in comps:
+        out += _native.line_integrals_adjoint(vs, np.ascontiguousarray(y[:, :, planes]), subset)
+    return out
+
+
+def synth_components(sc):
+    """The component families of a mashed scanner (None when bins are single LORs)."""
+    if not getattr(sc, "components", ()):
+        return None
+    import synth  # the family geometry is input description, shared by both sides
+    return synth.component_scanners(sc)
+
+
 def project(sc, x, subset=-1, mult=None):
     """P_i x (float64, full sinogram shape; bins outside subset i are 0)."""
     if subset >= 0 and bin_subsets(sc):
-        y = _native.line_integrals(sc, x, -1) * subset_mask(sc, subset)
+        y = _line_integrals(sc, x, -1) * subset_mask(sc, subset)
     else:
-        y = _native.line_integrals(sc, x, subset)
+        y = _line_integrals(sc, x, subset)
     if mult is not None:
         y *= mult
     return y
@@ -59,8 +90,8 @@ def backproject(sc, y, subset=-1, mult=None):
     if mult is not None:
         y = y * mult
     if subset >= 0 and bin_subsets(sc):
-        return _native.line_integrals_adjoint(sc, y * subset_mask(sc, subset), -1)
-    return _native.line_integrals_adjoint(sc, y, subset)
+        return _line_integrals_adjoint(sc, y * subset_mask(sc, subset), -1)
+    return _line_integrals_adjoint(sc, y, subset)
 
 
 # ----------------------------------------------------------------------------------------

@@ -29,7 +29,8 @@ from concurrent.futures import ThreadPoolExecutor
 import numpy as np
 
 __all__ = [
-    "Scanner", "config_2d", "config_3d", "config_3d_small", "config_mmr", "tiny_2d", "tiny_3d", "batch_geometries",
+    "Scanner", "config_2d", "config_3d", "config_3d_oblique", "config_3d_small", "config_mmr", "config_mmr_exact",
+    "tiny_2d", "tiny_3d", "tiny_mashed", "batch_geometries", "component_scanners",
     "Ellipsoid", "random_phantom", "voxelize", "analytic_projection", "smooth_multipliers",
     "side_image", "make_problem", "random_image", "random_sinogram", "subset_views",
 ]
@@ -55,6 +56,11 @@ class Scanner:
     n_subsets: int
     name: str = ""
     subset_kind: str = "views"  # "views": view-interleaved subsets; "bins": bin j in subset j mod m
+    # Exact mashing: per segment, the LOR components summed into its bins, each (dz_mm, q_lo,
+    # q_hi, step): plane q of the segment includes the component's LOR (axial separation dz_mm,
+    # the plane's mid-point) when q_lo <= q < q_hi and (q - q_lo) % step == 0.  Empty: every bin
+    # is the single LOR of its segment's seg_dz.
+    components: tuple = ()
 
     @property
     def n_planes(self) -> int:
@@ -92,6 +98,25 @@ class Scanner:
         return dataclasses.asdict(self)
 
 
+def component_scanners(g: Scanner):
+    """The LOR families of a scanner with mashed bins: one single-segment scanner per component
+    (its planes at the component's spacing and axial separation) with the sinogram planes it
+    adds to.  None when the bins are not mashed."""
+    if not g.components:
+        return None
+    out = []
+    p0 = 0
+    for gi, (n, z0, dzm) in enumerate(zip(g.seg_n, g.seg_zmid0, g.seg_dzmid)):
+        for dz, qlo, qhi, step in g.components[gi]:
+            qs = list(range(int(qlo), int(qhi), int(step)))
+            if qs:
+                vs = dataclasses.replace(g, seg_n=(len(qs),), seg_zmid0=(z0 + qlo * dzm,), seg_dzmid=(step * dzm,),
+                                         seg_dz=(float(dz),), components=(), name=f"{g.name}-comp")
+                out.append((vs, np.asarray([p0 + q for q in qs], np.int64)))
+        p0 += n
+    return out
+
+
 def subset_views(g: Scanner, i: int):
     """Views of the view-interleaved subset i (evenly spaced view angles)."""
     return list(range(i, g.n_views, g.n_subsets))
@@ -118,6 +143,51 @@ def config_3d(n_subsets: int = 21) -> Scanner:
     return Scanner(nx=128, ny=128, nz=64, vx=2.0, vy=2.0, vz=2.0, n_radial=128, d_radial=2.0,
                    n_views=180, radius=300.0, seg_n=(64,), seg_zmid0=(-63.0,), seg_dzmid=(2.0,),
                    seg_dz=(0.0,), n_subsets=n_subsets, name="cyl3d-128x128x64-180v128r64p")
+
+
+def config_3d_oblique(n_subsets: int = 21) -> Scanner:
+    """The 3-D configuration with its adjacent-oblique planes summed exactly: plane p is the direct
+    LOR of ring p plus the two LORs of rings (p-1, p+1) and (p+1, p-1), which share its axial
+    centre (ring difference +-2, i.e. +-4 mm with 2 mm rings; only the direct LOR at the two edge
+    planes)."""
+    g = config_3d(n_subsets)
+    ring = 2.0
+    comps = ((0.0, 0, 64, 1), (2 * ring, 1, 63, 1), (-2 * ring, 1, 63, 1))
+    return dataclasses.replace(g, components=(comps,), name="cyl3d-oblique-128x128x64-180v128r64p")
+
+
+def tiny_mashed(n_subsets: int = 2) -> Scanner:
+    """The steep tiny scanner with mashed bins: each plane of the direct segment sums its direct
+    LOR and, on its three inner planes, two LORs tilted by +-1 mm; the oblique segments hold
+    LORs of two tilts on alternating planes (the range and parity rules of exact mashing)."""
+    g = tiny_3d(n_subsets, steep=True)
+    c0 = ((0.0, 0, 5, 1), (1.0, 1, 4, 1), (-1.0, 1, 4, 1))
+    c1 = ((8.0, 0, 4, 2), (6.0, 1, 4, 2))
+    c2 = ((-8.0, 0, 4, 2), (-6.0, 1, 4, 2))
+    return dataclasses.replace(g, components=(c0, c1, c2), name="tiny3d-mashed")
+
+
+MMR_SPAN11_DIFFS = ((-5, 5), (6, 16), (-16, -6), (17, 27), (-27, -17), (28, 38), (-38, -28), (39, 49),
+                    (-49, -39), (50, 60), (-60, -50))
+
+
+def config_mmr_exact(n_subsets: int = 252) -> Scanner:
+    """The mMR-like scanner with exact span-11 mashing: a bin of segment g at ring sum s sums the
+    LORs of every ring pair (r1, r2) with r1 + r2 = s and r1 - r2 in the segment's ring-difference
+    range (64 rings; ring difference d has ring sums |d| .. 126 - |d| of d's parity)."""
+    g = config_mmr(n_subsets)
+    ring_pitch = 2.0 * g.vz
+    comps = []
+    for (first, n, _), (d_lo, d_hi) in zip(MMR_SPAN11_SEGMENTS, MMR_SPAN11_DIFFS):
+        cs = []
+        for d in range(d_lo, d_hi + 1):
+            s_lo, s_hi = abs(d), 126 - abs(d)          # ring sums of the pairs with this difference
+            q_lo, q_hi = s_lo - first, s_hi - first + 1
+            q_lo, q_hi = max(q_lo, 0), min(q_hi, n)
+            if q_lo < q_hi:
+                cs.append((d * ring_pitch, q_lo, q_hi, 2))
+        comps.append(tuple(cs))
+    return dataclasses.replace(g, components=tuple(comps), name="mmr-exact-span11-344x344x127-252v344r837p")
 
 
 def config_3d_small(n_subsets: int = 8) -> Scanner:
@@ -327,7 +397,14 @@ def _project_views(g: Scanner, ells, v0: int, v1: int):
 
 
 def analytic_projection(g: Scanner, ells, threads: int = 0):
-    """Exact line integrals of the continuous phantom along every LOR (voxel-size units)."""
+    """Exact line integrals of the continuous phantom along every LOR (voxel-size units); a
+    mashed bin holds the sum over its LOR components."""
+    comps = component_scanners(g)
+    if comps is not None:
+        out = np.zeros(g.sino_shape, np.float64)
+        for vs, planes in comps:
+            out[:, :, planes] += analytic_projection(vs, ells, threads)
+        return out
     out = np.empty(g.sino_shape, np.float64)
     workers = threads or min(32, max(1, (__import__("os").cpu_count() or 1)))
     group = max(1, min(g.n_views, (1 << 18) // max(1, g.n_radial * g.n_planes)))
