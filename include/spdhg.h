@@ -72,6 +72,19 @@ typedef struct {
   const double* seg_dzmid;    /* plane spacing within the segment; must equal vz if seg_n > 1 */
   const double* seg_dz;       /* axial separation z2 - z1 of the segment's LOR ends, mm */
   int n_subsets;              /* m, number of data subsets */
+  int n_components;           /* exact mashing (0: none, every bin is the single LOR of its segment,
+                                 seg_dz): the LOR components summed into the bins.  Component c
+                                 belongs to segment comp_seg[c] (non-decreasing; every segment has
+                                 at least one); plane q of that segment includes its LOR (the
+                                 plane's mid-point, axial separation comp_dz[c] mm) when
+                                 comp_qlo[c] <= q < comp_qhi[c] and (q - comp_qlo[c]) is a
+                                 multiple of comp_step[c] (1 or 2).  Span-11 data are mashed this
+                                 way from the ring-pair LORs of span 1 (Sec. 1) */
+  const int* comp_seg;
+  const double* comp_dz;
+  const int* comp_qlo;
+  const int* comp_qhi;
+  const int* comp_step;
   int subset_kind;            /* SPDHG_SUBSETS_VIEWS (0): subset i = views v with v mod m == i;
                                  SPDHG_SUBSETS_BINS (1): subset i = bins j of the flattened sinogram
                                  with j mod m == i (the equidistantly divided bins of the stability
@@ -139,8 +152,9 @@ typedef struct {
 
 /* Creates a context for a geometry on the current CUDA device (device tables, no data yet).
  * Fails with SPDHG_ERR_UNSUPPORTED when vx != vy, when a multi-plane segment's spacing differs
- * from vz, when radius <= max |s|, or when an oblique LOR crosses more than 4 slices inside one
- * transaxial pixel.  *out receives the context (NULL on failure). */
+ * from vz, when radius <= max |s|, when an oblique LOR crosses more than 4 slices inside one
+ * transaxial pixel, or when a segment has more than 32 components.  *out receives the context
+ * (NULL on failure). */
 int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out);
 
 /* Releases every device buffer of the context.  NULL is accepted. */

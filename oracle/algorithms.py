@@ -73,6 +73,36 @@ def synth_components(sc):
     return synth.component_scanners(sc)
 
 
+def project_at_bins(sc, x, bins):
+    """(L x) at the given flattened bin indices (no multiplier), by the definition: for a mashed
+    scanner the sum over the LOR components each bin's plane includes."""
+    bins = np.asarray(bins, np.int64)
+    comps = synth_components(sc)
+    if comps is None:
+        return _native.line_integrals_at(sc, x, bins)
+    V, R, P = sc.sino_shape
+    v, r, p = np.unravel_index(bins, (V, R, P))
+    out = np.zeros(len(bins))
+    for vs, planes in comps:
+        where = {int(pl): k for k, pl in enumerate(planes)}
+        sel = np.nonzero(np.isin(p, planes))[0]
+        if sel.size:
+            vb = np.ravel_multi_index((v[sel], r[sel], np.array([where[int(q)] for q in p[sel]])), vs.sino_shape)
+            out[sel] += _native.line_integrals_at(vs, x, vb)
+    return out
+
+
+def backproject_at_voxels(sc, y, voxels, subset=-1):
+    """(L_subset^T y) at the given flattened voxel indices (no multiplier), by the definition."""
+    comps = synth_components(sc)
+    if comps is None:
+        return _native.adjoint_at_voxels(sc, y, voxels, subset)
+    out = np.zeros(len(voxels))
+    for vs, planes in comps:
+        out += _native.adjoint_at_voxels(vs, np.ascontiguousarray(np.asarray(y)[:, :, planes]), voxels, subset)
+    return out
+
+
 def project(sc, x, subset=-1, mult=None):
     """P_i x (float64, full sinogram shape; bins outside subset i are 0)."""
     if subset >= 0 and bin_subsets(sc):

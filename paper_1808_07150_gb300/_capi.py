@@ -49,7 +49,10 @@ class Geometry(ctypes.Structure):
         ("radius", ctypes.c_double), ("n_segments", ctypes.c_int),
         ("seg_n", ctypes.POINTER(ctypes.c_int)), ("seg_zmid0", ctypes.POINTER(ctypes.c_double)),
         ("seg_dzmid", ctypes.POINTER(ctypes.c_double)), ("seg_dz", ctypes.POINTER(ctypes.c_double)),
-        ("n_subsets", ctypes.c_int), ("subset_kind", ctypes.c_int),
+        ("n_subsets", ctypes.c_int), ("n_components", ctypes.c_int),
+        ("comp_seg", ctypes.POINTER(ctypes.c_int)), ("comp_dz", ctypes.POINTER(ctypes.c_double)),
+        ("comp_qlo", ctypes.POINTER(ctypes.c_int)), ("comp_qhi", ctypes.POINTER(ctypes.c_int)),
+        ("comp_step", ctypes.POINTER(ctypes.c_int)), ("subset_kind", ctypes.c_int),
     ]
 
 
@@ -154,9 +157,17 @@ def make_geometry(sc):
     n = len(sc.seg_n)
     keep = [(ctypes.c_int * n)(*sc.seg_n), (ctypes.c_double * n)(*sc.seg_zmid0),
             (ctypes.c_double * n)(*sc.seg_dzmid), (ctypes.c_double * n)(*sc.seg_dz)]
+    comps = [(k, c) for k, cs in enumerate(getattr(sc, "components", ()) or ()) for c in cs]
+    nc = len(comps)
+    ck = [(ctypes.c_int * max(nc, 1))(*[k for k, _ in comps]),
+          (ctypes.c_double * max(nc, 1))(*[float(c[0]) for _, c in comps]),
+          (ctypes.c_int * max(nc, 1))(*[int(c[1]) for _, c in comps]),
+          (ctypes.c_int * max(nc, 1))(*[int(c[2]) for _, c in comps]),
+          (ctypes.c_int * max(nc, 1))(*[int(c[3]) for _, c in comps])]
+    keep += ck
     g = Geometry(sc.nx, sc.ny, sc.nz, sc.vx, sc.vy, sc.vz, sc.n_radial, sc.d_radial, sc.n_views,
-                 sc.radius, n, keep[0], keep[1], keep[2], keep[3], sc.n_subsets,
-                 SUBSETS[getattr(sc, "subset_kind", "views")])
+                 sc.radius, n, keep[0], keep[1], keep[2], keep[3], sc.n_subsets, nc,
+                 ck[0], ck[1], ck[2], ck[3], ck[4], SUBSETS[getattr(sc, "subset_kind", "views")])
     return g, keep
 
 

@@ -389,8 +389,49 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
     if (g.seg_n[k] < 1) return SPDHG_ERR_ARG;
     if (g.seg_n[k] > 1 && fabs(g.seg_dzmid[k] - g.vz) > 1e-9 * g.vz) return SPDHG_ERR_UNSUPPORTED;
     P += g.seg_n[k];
-    kappa_max = std::max(kappa_max, fabs(g.seg_dz[k]) / (2.0 * hmin * g.vz));
   }
+  // LOR components: the given ones (exact mashing), or one per segment covering every plane
+  std::vector<int> c_seg, c_qlo, c_qhi, c_step;
+  std::vector<double> c_dz;
+  if (g.n_components > 0) {
+    if (!g.comp_seg || !g.comp_dz || !g.comp_qlo || !g.comp_qhi || !g.comp_step) return SPDHG_ERR_ARG;
+    int prev = 0;
+    std::vector<int> per_seg(g.n_segments, 0);
+    for (int c = 0; c < g.n_components; ++c) {
+      const int k = g.comp_seg[c];
+      if (k < prev || k >= g.n_segments || g.comp_qlo[c] < 0 || g.comp_qhi[c] > g.seg_n[k] ||
+          g.comp_qlo[c] >= g.comp_qhi[c] || (g.comp_step[c] != 1 && g.comp_step[c] != 2) || !isfinite(g.comp_dz[c]))
+        return SPDHG_ERR_ARG;
+      prev = k;
+      if (++per_seg[k] > 32) return SPDHG_ERR_UNSUPPORTED;
+      c_seg.push_back(k);
+      c_dz.push_back(g.comp_dz[c]);
+      c_qlo.push_back(g.comp_qlo[c]);
+      c_qhi.push_back(g.comp_qhi[c]);
+      c_step.push_back(g.comp_step[c]);
+    }
+    for (int k = 0; k < g.n_segments; ++k)
+      if (per_seg[k] == 0) return SPDHG_ERR_ARG;
+  } else {
+    for (int k = 0; k < g.n_segments; ++k) {
+      c_seg.push_back(k);
+      c_dz.push_back(g.seg_dz[k]);
+      c_qlo.push_back(0);
+      c_qhi.push_back(g.seg_n[k]);
+      c_step.push_back(1);
+    }
+  }
+  const int C = (int)c_seg.size();
+  bool mashed = false;
+  {
+    std::vector<int> per_seg(g.n_segments, 0);
+    for (int c = 0; c < C; ++c) {
+      ++per_seg[c_seg[c]];
+      if (c_qlo[c] != 0 || c_qhi[c] != g.seg_n[c_seg[c]] || c_step[c] != 1) mashed = true;
+    }
+    for (int k = 0; k < g.n_segments; ++k) mashed = mashed || per_seg[k] > 1;
+  }
+  for (int c = 0; c < C; ++c) kappa_max = std::max(kappa_max, fabs(c_dz[c]) / (2.0 * hmin * g.vz));
   if (P > 8192) return SPDHG_ERR_UNSUPPORTED;
   // kernels index images (up to 6 components) and sinograms with 32-bit integers
   if ((double)g.nx * g.ny * g.nz * 6 >= 2147483647.0 || (double)g.n_views * g.n_radial * P >= 2147483647.0)
@@ -411,6 +452,17 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   ctx->geom.seg_zmid0 = ctx->seg_zmid0.data();
   ctx->geom.seg_dzmid = ctx->seg_dzmid.data();
   ctx->geom.seg_dz = ctx->seg_dz.data();
+  ctx->comp_seg = c_seg;
+  ctx->comp_dz = c_dz;
+  ctx->comp_qlo = c_qlo;
+  ctx->comp_qhi = c_qhi;
+  ctx->comp_step = c_step;
+  ctx->geom.n_components = g.n_components > 0 ? C : 0;
+  ctx->geom.comp_seg = g.n_components > 0 ? ctx->comp_seg.data() : nullptr;
+  ctx->geom.comp_dz = g.n_components > 0 ? ctx->comp_dz.data() : nullptr;
+  ctx->geom.comp_qlo = g.n_components > 0 ? ctx->comp_qlo.data() : nullptr;
+  ctx->geom.comp_qhi = g.n_components > 0 ? ctx->comp_qhi.data() : nullptr;
+  ctx->geom.comp_step = g.n_components > 0 ? ctx->comp_step.data() : nullptr;
   cudaGetDevice(&ctx->device);
   ctx->N = (int64_t)g.nx * g.ny * g.nz;
   ctx->M = (int64_t)g.n_views * g.n_radial * P;
@@ -430,7 +482,7 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
     lo = (float)(v - (double)hi);
   };
   const int R = g.n_radial, V = g.n_views, S = g.n_segments;
-  std::vector<float4> view(V), rad(R), rs((size_t)R * S);
+  std::vector<float4> view(V), rad(R), rs((size_t)R * C);
   std::vector<float2> view_inv(V);
   for (int v = 0; v < V; ++v) {
     double c = cos(pi * v / V), sn = sin(pi * v / V);
@@ -450,45 +502,50 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
     split(s / g.vx, t.x, t.y);
     split(h / g.vx, t.z, t.w);
     rad[r] = t;
-    for (int k = 0; k < S; ++k) {
-      const double slope = g.seg_dz[k] / (2.0 * h);  // dz/dt of the LOR
+    for (int c = 0; c < C; ++c) {
+      const double slope = c_dz[c] / (2.0 * h);      // dz/dt of the component's LOR
       float4 u;
       split(slope * g.vx / g.vz, u.x, u.y);          // slab units per pixel unit of t
       u.z = (float)sqrt(1.0 + slope * slope);        // 3-D length per transaxial length
       u.w = 0.f;
-      rs[(size_t)r * S + k] = u;
+      rs[(size_t)r * C + c] = u;
     }
   }
   const double loz = -0.5 * g.nz * g.vz;
   std::vector<SegDev> seg(S);
+  std::vector<CompDev> comp(C);
   std::vector<int> plane_seg(P);
   int p0 = 0;
   int fz_lo = taps - 1, fz_stride = g.nz;
   for (int k = 0; k < S; ++k) {
     seg[k].p0 = p0;
     seg[k].n = g.seg_n[k];
-    const double f = (g.seg_zmid0[k] - loz) / g.vz;
-    split(f, seg[k].f_hi, seg[k].f_lo);
-    // Axial bound of the forward gather: along the LOR of plane 0 the slab coordinate is
-    // f + kappa t with |t| <= h, so every slab it touches lies in [floor(f - |kappa| h),
-    // floor(f + |kappa| h)]; the tap offset j0 (plane 0's top slab is -j0) lies within that range
-    // widened by two slabs for rounding.  The staged columns get frames that hold every read.
-    double zlo = f, zhi = f;
-    for (int r = 0; r < R; ++r) {
-      const double s_r = (r - 0.5 * (R - 1)) * g.d_radial;
-      const double h = sqrt(g.radius * g.radius - s_r * s_r);
-      const double span = fabs(g.seg_dz[k]) / (2.0 * h) * h / g.vz;  // |kappa| h in slabs
-      zlo = std::min(zlo, f - span);
-      zhi = std::max(zhi, f + span);
-    }
-    seg[k].jlo = -(int)floor(zhi) - 2;
-    seg[k].jhi = -(int)floor(zlo) + 2;
-    fz_lo = std::max(fz_lo, seg[k].jhi + taps - 1);
+    split((g.seg_zmid0[k] - loz) / g.vz, seg[k].f_hi, seg[k].f_lo);
+    seg[k].c0 = -1;
+    seg[k].nc = 0;
     for (int q = 0; q < g.seg_n[k]; ++q) plane_seg[p0 + q] = k;
     p0 += g.seg_n[k];
   }
+  for (int c = 0; c < C; ++c) {
+    const int k = c_seg[c];
+    if (seg[k].c0 < 0) seg[k].c0 = c;
+    ++seg[k].nc;
+    comp[c].seg = k;
+    comp[c].qlo = c_qlo[c];
+    comp[c].qhi = c_qhi[c];
+    comp[c].smask = c_step[c] - 1;
+    // Axial bound of the forward gather: along the component's LOR of plane 0 the slab coordinate
+    // is f + kappa t with |t| <= h, so every slab it touches lies in [floor(f - |kappa| h),
+    // floor(f + |kappa| h)]; the tap offset j0 (plane 0's top slab is -j0) lies within that range
+    // widened by two slabs for rounding.  The staged columns get frames that hold every read.
+    const double f = (g.seg_zmid0[k] - loz) / g.vz;
+    const double span = fabs(c_dz[c]) / (2.0 * g.vz);  // |kappa| h in slabs (independent of h)
+    comp[c].jlo = -(int)floor(f + span) - 2;
+    comp[c].jhi = -(int)floor(f - span) + 2;
+    fz_lo = std::max(fz_lo, comp[c].jhi + taps - 1);
+  }
   // plane q (read as min(q, n - 1)) reads slabs q - j0 - t: the highest is n - 1 - jlo
-  for (int k = 0; k < S; ++k) fz_stride = std::max(fz_stride, g.seg_n[k] + 3 - seg[k].jlo);
+  for (int c = 0; c < C; ++c) fz_stride = std::max(fz_stride, g.seg_n[c_seg[c]] + 3 - comp[c].jlo);
   fz_stride += fz_lo;
   fz_stride = std::max(fz_stride, fz_lo + g.nz);
   std::vector<int2> runs;
@@ -501,12 +558,14 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   cudaError_t e;
   if ((e = cudaMalloc(&ctx->d_view, sizeof(float4) * V)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMalloc(&ctx->d_rad, sizeof(float4) * R)) != cudaSuccess) return cleanup_fail(e);
-  if ((e = cudaMalloc(&ctx->d_rs, sizeof(float4) * R * S)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMalloc(&ctx->d_rs, sizeof(float4) * R * C)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMalloc(&ctx->d_comp, sizeof(CompDev) * C)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMemcpy(ctx->d_comp, comp.data(), sizeof(CompDev) * C, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMalloc(&ctx->d_seg, sizeof(SegDev) * S)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMalloc(&ctx->d_plane_seg, sizeof(int) * P)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_view, view.data(), sizeof(float4) * V, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_rad, rad.data(), sizeof(float4) * R, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
-  if ((e = cudaMemcpy(ctx->d_rs, rs.data(), sizeof(float4) * R * S, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMemcpy(ctx->d_rs, rs.data(), sizeof(float4) * R * C, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_seg, seg.data(), sizeof(SegDev) * S, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_plane_seg, plane_seg.data(), sizeof(int) * P, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMalloc(&ctx->d_runs, sizeof(int2) * runs.size())) != cudaSuccess) return cleanup_fail(e);
@@ -524,6 +583,9 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   d.m = g.n_subsets;
   d.bins = g.subset_kind == SPDHG_SUBSETS_BINS ? 1 : 0;
   d.n_seg = S;
+  d.n_comp = C;
+  d.mashed = mashed ? 1 : 0;
+  d.comp = ctx->d_comp;
   d.taps = taps;
   d.nr_max = nr_max;
   d.half_R = (float)(0.5 * (R - 1));
@@ -536,6 +598,17 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   d.plane_seg = ctx->d_plane_seg;
   d.n_runs = (int)runs.size();
   d.runs = ctx->d_runs;
+  for (int w = 0; w <= 16; ++w) {
+    // components spanned by the blocks of the forward projector with w warps (2 runs each)
+    int mx = 1;
+    const int rpp = 2 * std::max(w, 1);
+    for (size_t r0 = 0; r0 < runs.size(); r0 += rpp) {
+      const size_t r1 = std::min(runs.size(), r0 + rpp) - 1;
+      const int glo = runs[r0].x, ghi = runs[r1].x;
+      mx = std::max(mx, seg[ghi].c0 + seg[ghi].nc - seg[glo].c0);
+    }
+    d.max_part_comps[w] = mx;
+  }
   d.fz_lo = fz_lo;
   d.fz_stride = fz_stride;
   *out = ctx;
@@ -544,7 +617,7 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
 
 void spdhg_destroy(spdhg_ctx* ctx) {
   if (!ctx) return;
-  void* ptrs[] = {ctx->d_view, ctx->d_view_inv, ctx->d_rad, ctx->d_rs, ctx->d_runs, ctx->d_seg, ctx->d_plane_seg, ctx->b, ctx->r, ctx->mult, ctx->side,
+  void* ptrs[] = {ctx->d_view, ctx->d_view_inv, ctx->d_rad, ctx->d_rs, ctx->d_runs, ctx->d_seg, ctx->d_comp, ctx->d_plane_seg, ctx->b, ctx->r, ctx->mult, ctx->side,
                   ctx->x[0], ctx->x[1], ctx->z, ctx->T, ctx->y, ctx->sigma, ctx->wdy, ctx->q[0], ctx->q[1],
                   ctx->w[0], ctx->w[1], ctx->zw, ctx->q2[0], ctx->q2[1], ctx->tgv_b, ctx->tmp_sino, ctx->tmp_img, ctx->tmp_img2, ctx->em_sens, ctx->fwd_part, ctx->fwd_tickets,
                   ctx->red, ctx->red_out};

@@ -21,7 +21,16 @@ struct SegDev {
   int p0;      // first plane index of the segment in the sinogram
   int n;       // planes in the segment
   float f_hi, f_lo;
-  int jlo, jhi;  // range of the tap offset j0 of any pixel of any LOR of the segment (host bound)
+  int c0, nc;  // the segment's LOR components: c0 .. c0 + nc - 1
+};
+
+// One LOR component of a segment's bins (exact mashing; without mashing every segment has one
+// component that every plane includes).  Plane q of the segment includes it when
+// qlo <= q < qhi and ((q - qlo) & smask) == 0 (step 1: smask 0, step 2: smask 1).
+struct CompDev {
+  int seg;
+  int qlo, qhi, smask;
+  int jlo, jhi;  // range of the tap offset j0 of any pixel of any LOR of the component (host bound)
 };
 
 // Geometry passed by value to every kernel.  Transaxial quantities are in pixel units (mm / vx);
@@ -32,6 +41,8 @@ struct DevGeom {
   int R, V, P, m;        // radial bins, views, planes, subsets
   int bins;              // 1: bin-interleaved subsets (every subset spans all views), 0: view subsets
   int n_seg;
+  int n_comp;            // LOR components (= n_seg without mashing)
+  int mashed;            // 1: some bin sums several LORs or some plane lacks a component
   int taps;              // maximum slices a LOR crosses inside one pixel
   int nr_max;            // maximum candidate radial bins per pixel and view
   float half_R;          // (R - 1) / 2
@@ -39,11 +50,13 @@ struct DevGeom {
   const float4* view;    // per view: cos_hi, cos_lo, sin_hi, sin_lo (exact zeros on the axes)
   const float2* view_inv;  // per view: 1 / (-sin_hi), 1 / cos_hi (0 where the component is 0)
   const float4* rad;     // per radial bin: s_hi, s_lo, h_hi, h_lo (s = signed offset, h = half chord)
-  const float4* rs;      // per (radial bin, segment): kappa_hi, kappa_lo, len_scale, 0
+  const float4* rs;      // per (radial bin, component): kappa_hi, kappa_lo, len_scale, 0
   const SegDev* seg;
+  const CompDev* comp;
   const int* plane_seg;  // plane -> segment
   int n_runs;            // plane runs of the forward projector: run k = planes [q0, q0 + 32) of one segment
   const int2* runs;      // (segment, q0) per run, segment-major
+  int max_part_comps[17];  // forward: most components one block spans, by warps per block
   int fz_lo;             // forward staging: zero slabs below each staged x column
   int fz_stride;         // forward staging: floats per staged x column (frames included)
   int tune[SPDHG_TUNE_KNOBS];  // launch-shape overrides (0: built-in heuristic)
@@ -209,6 +222,8 @@ struct spdhg_ctx {
   spdhg_geometry geom{};
   std::vector<int> seg_n;
   std::vector<double> seg_zmid0, seg_dzmid, seg_dz;
+  std::vector<int> comp_seg, comp_qlo, comp_qhi, comp_step;
+  std::vector<double> comp_dz;
   spdhg::DevGeom dg{};
   int64_t N = 0, M = 0, max_subset_bins = 0;
   int device = 0;
@@ -219,6 +234,7 @@ struct spdhg_ctx {
   int2* d_runs = nullptr;
   float2* d_view_inv = nullptr;
   spdhg::SegDev* d_seg = nullptr;
+  spdhg::CompDev* d_comp = nullptr;
   int* d_plane_seg = nullptr;
   // data
   float *b = nullptr, *r = nullptr, *mult = nullptr, *side = nullptr;

@@ -96,14 +96,15 @@ __device__ __forceinline__ bool pixel_interval(const DevGeom& g, const Line& L, 
   return hi > lo;
 }
 
-// Lengths (voxel units) of the plane-q LOR of segment gi in slabs iz = q - (j0 + k), k < NT,
+// Lengths (voxel units) of the plane-q LOR of component ci in slabs iz = q - (j0 + k), k < NT,
 // inside the pixel interval I.  The LOR's slab coordinate at the foot point,
 // zeta_c = f + kappa tc, is split exactly into an integer n0 and a fraction in [0, 1); the
 // crossings are then solved in local quantities of order one.  Returns j0.
 template <int NT>
-__device__ __forceinline__ int segment_taps(const DevGeom& g, int r, int gi, const PixInt& I, float* Lk) {
-  const float4 rs = g.rs[r * g.n_seg + gi];
-  const SegDev sd = g.seg[gi];
+__device__ __forceinline__ int segment_taps(const DevGeom& g, int r, int ci, const PixInt& I, float* Lk) {
+  // ci: the LOR component (its axial tilt); the plane mid-points are those of its segment
+  const float4 rs = g.rs[r * g.n_comp + ci];
+  const SegDev sd = g.seg[g.comp[ci].seg];
   const float kh = rs.x, kl = rs.y, scale = rs.z;
   float p, e, s1, e1;
   two_prod(kh, I.tch, p, e);
@@ -199,7 +200,7 @@ __device__ __forceinline__ int row_entries(const DevGeom& g, const Line& L, bool
   return n;
 }
 
-constexpr int kFwdChunk = 16;  // pixel entries per double-buffered chunk
+constexpr int kFwdChunk = 32;  // pixel entries per double-buffered chunk
 constexpr int kRunsPerWarp = 2;  // 32-plane runs per warp (lane = plane within a run)
 
 // Block-wide exclusive prefix sum of one int per thread (blockDim <= 1024); returns the
@@ -281,14 +282,14 @@ __device__ __forceinline__ float taps_dot(const Rec& t, int nt, const float* xp,
 // reduces them in a fixed order.
 template <int NT, int MODE>
 __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap, int rsplit, int xs_stride,
-                                                 int runs_per_part, int nseg_tab, FwdArgs a) {
+                                                 int runs_per_part, int ncomp_tab, int chunk, FwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int scan_scratch[33];
   const int FL = g.fz_lo;
-  float* xs = reinterpret_cast<float*>(smem);                                  // [2][kFwdChunk][xs_stride]
+  float* xs = reinterpret_cast<float*>(smem);                                  // [2][chunk][xs_stride]
   using Rec = TapRecT<NT>;
-  Rec* taps = reinterpret_cast<Rec*>(xs + 2 * kFwdChunk * xs_stride);          // [2][nseg_tab][kFwdChunk]
-  Entry* ent = reinterpret_cast<Entry*>(taps + 2 * nseg_tab * kFwdChunk);      // [ecap]
+  Rec* taps = reinterpret_cast<Rec*>(xs + 2 * chunk * xs_stride);              // [2][ncomp_tab][chunk]
+  Entry* ent = reinterpret_cast<Entry*>(taps + 2 * ncomp_tab * chunk);         // [ecap]
   const int nz = g.nz;
 
   const int line = blockIdx.x, rpart = blockIdx.y, ppart = blockIdx.z;
@@ -301,7 +302,10 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
   const int rfirst = ppart * runs_per_part;
   const int rlast = min(g.n_runs, rfirst + runs_per_part) - 1;
   const int g_lo = g.runs[rfirst].x, g_hi = g.runs[rlast].x;
+  // the LOR components of the block's segments, c_lo .. c_hi
+  const int c_lo = g.seg[g_lo].c0, c_hi = g.seg[g_hi].c0 + g.seg[g_hi].nc - 1;
   int gs_[kRunsPerWarp], qv_[kRunsPerWarp], qr_[kRunsPerWarp];
+  unsigned incl_[kRunsPerWarp];                  // mashed: components of the segment this plane sums
   bool valid_[kRunsPerWarp];
 #pragma unroll
   for (int k = 0; k < kRunsPerWarp; ++k) {
@@ -312,12 +316,19 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
     qv_[k] = ru.y + lane;                        // the plane of this lane
     valid_[k] = run <= rlast && qv_[k] < sd.n;
     qr_[k] = min(qv_[k], sd.n - 1);              // the plane read (inside the segment's frames)
+    incl_[k] = 0u;
+    if (g.mashed)
+      for (int c = 0; c < sd.nc; ++c) {
+        const CompDev cd = g.comp[sd.c0 + c];
+        const int dq = qv_[k] - cd.qlo;
+        if (qv_[k] < cd.qhi && dq >= 0 && (dq & cd.smask) == 0) incl_[k] |= 1u << c;
+      }
   }
   const bool same = gs_[0] == gs_[1];            // warp-uniform
 
   // zero frames of the staged columns (never overwritten); SIGMA stages ones: the projection of
   // the constant image is the chord of each LOR inside the image
-  for (int i = threadIdx.x; i < 2 * kFwdChunk * xs_stride; i += blockDim.x) {
+  for (int i = threadIdx.x; i < 2 * chunk * xs_stride; i += blockDim.x) {
     const int k = i % xs_stride;
     if (MODE == FWD_SIGMA) xs[i] = (k >= FL && k < FL + nz) ? 1.f : 0.f;
     else if (k < FL || k >= FL + nz) xs[i] = 0.f;
@@ -341,11 +352,11 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
   }
   __syncthreads();
 
-  const int nsb = g_hi - g_lo + 1;
+  const int ncb = c_hi - c_lo + 1;
   auto stage = [&](int c) {  // x columns + taps of chunk c into buffer c & 1
     const int buf = c & 1;
-    const int e0 = c * kFwdChunk, ne = min(kFwdChunk, n_ent - e0);
-    float* xb = xs + buf * kFwdChunk * xs_stride;
+    const int e0 = c * chunk, ne = min(chunk, n_ent - e0);
+    float* xb = xs + buf * chunk * xs_stride;
     if (MODE != FWD_SIGMA) {
       // one warp per entry, lanes along z
       for (int e = wi; e < ne; e += nw) {
@@ -355,18 +366,18 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
       }
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
-    Rec* tb = taps + buf * nseg_tab * kFwdChunk;
-    for (int it = threadIdx.x; it < nsb * ne; it += blockDim.x) {
+    Rec* tb = taps + buf * ncomp_tab * chunk;
+    for (int it = threadIdx.x; it < ncb * ne; it += blockDim.x) {
       const int gs = it / ne, e = it - gs * ne;
       float Lk[4] = {0.f, 0.f, 0.f, 0.f};
-      int j0 = segment_taps<NT>(g, r, g_lo + gs, ent[e0 + e].I, Lk);
+      int j0 = segment_taps<NT>(g, r, c_lo + gs, ent[e0 + e].I, Lk);
       // the geometry's axial bound keeps every read inside the framed column; the clamp only
       // guards shared memory should a rounding case fall outside it
-      const SegDev sd = g.seg[g_lo + gs];
-      j0 = min(max(j0, sd.jlo), sd.jhi);
+      const CompDev cd = g.comp[c_lo + gs];
+      j0 = min(max(j0, cd.jlo), cd.jhi);
       int nt = NT;
       while (nt > 1 && Lk[nt - 1] == 0.f) --nt;
-      Rec& rec = tb[gs * kFwdChunk + e];
+      Rec& rec = tb[gs * chunk + e];
       rec.l0 = Lk[0];
       rec.l1 = NT > 1 ? Lk[1] : 0.f;
       rec.l2 = NT > 2 ? Lk[2] : 0.f;
@@ -376,7 +387,7 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
   };
 
   float acc[kRunsPerWarp] = {0.f, 0.f};
-  const int nchunks = (n_ent + kFwdChunk - 1) / kFwdChunk;
+  const int nchunks = (n_ent + chunk - 1) / chunk;
   if (nchunks > 0) stage(0);
   for (int c = 0; c < nchunks; ++c) {
     if (c + 1 < nchunks) {
@@ -387,12 +398,34 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
     }
     __syncthreads();
     const int buf = c & 1;
-    const int ne = min(kFwdChunk, n_ent - c * kFwdChunk);
-    const float* xb = xs + buf * kFwdChunk * xs_stride;
-    const Rec* tr0 = taps + buf * nseg_tab * kFwdChunk + (gs_[0] - g_lo) * kFwdChunk;
+    const int ne = min(chunk, n_ent - c * chunk);
+    const float* xb = xs + buf * chunk * xs_stride;
+    if (g.mashed) {
+      // each plane sums the components of its segment it includes (exact mashing)
+#pragma unroll
+      for (int k = 0; k < kRunsPerWarp; ++k) {
+        const SegDev sd = g.seg[gs_[k]];
+        const Rec* trk = taps + buf * ncomp_tab * chunk + (sd.c0 - c_lo) * chunk;
+        float sk = 0.f;
+        for (int ci = 0; ci < sd.nc; ++ci) {
+          const bool in = (incl_[k] >> ci) & 1u;
+          const Rec* tc = trk + ci * chunk;
+          float sc = 0.f;
+          for (int e = 0; e < ne; ++e) {
+            const Rec t = tc[e];
+            sc = taps_dot<NT>(t, NT > 1 ? (t.off >> kOffBits) : 1, xb + (t.off & kOffMask) + qr_[k], sc);
+          }
+          sk += in ? sc : 0.f;
+        }
+        acc[k] += sk;
+      }
+      __syncthreads();
+      continue;
+    }
+    const Rec* tr0 = taps + buf * ncomp_tab * chunk + (gs_[0] - g_lo) * chunk;
     if (same) {
       float2 s2 = make_float2(0.f, 0.f);
-#pragma unroll 2
+#pragma unroll 1
       for (int e = 0; e < ne; ++e) {
         const Rec t = tr0[e];
         const int off = t.off & kOffMask, nt = NT > 1 ? (t.off >> kOffBits) : 1;
@@ -412,7 +445,7 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
       acc[0] += s2.x;
       acc[1] += s2.y;
     } else {
-      const Rec* tr1 = taps + buf * nseg_tab * kFwdChunk + (gs_[1] - g_lo) * kFwdChunk;
+      const Rec* tr1 = taps + buf * ncomp_tab * chunk + (gs_[1] - g_lo) * chunk;
       float s0 = 0.f, s1 = 0.f;
       for (int e = 0; e < ne; ++e) {
         const Rec t0 = tr0[e], t1 = tr1[e];
@@ -510,9 +543,9 @@ constexpr int kBwdMaxItems = 64;         // (pair, segment) items per column and
 // compute the axial taps of every (pair, segment) item, and then gather along contiguous plane
 // runs from shared memory, lane = iz mod 32, ZK voxels per lane.  Up to 128 slices (ZK <= 4) four
 // blocks share an SM (32 registers per thread); with eight accumulators per lane, three.
-template <int NT, int ZK, int MODE>
+template <int NT, int ZK, int MODE, bool MASHED>
 __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(DevGeom g, int subset, int nr_tile, int p_pad,
-                                                             int bcap, BwdArgs a) {
+                                                             int bcap, int cpb, BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int PAD = NT - 1;
   const int icap = bcap;  // items per warp (all buckets)
@@ -522,6 +555,11 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
   PixItem* pix = reinterpret_cast<PixItem*>(itM + kBwdWarps * icap);          // [warp][nr_max]
   int* seg_of = reinterpret_cast<int*>(pix + kBwdWarps * g.nr_max);           // [P]: padded position
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  float4* myL = itL + wi * icap;
+  int4* myM = itM + wi * icap;
+  PixItem* mypix = pix + wi * g.nr_max;
+  const int nviews = subset_views(g, subset);
+  const int nz = g.nz;
   const int tx0 = blockIdx.x * kBwdTile, ty0 = blockIdx.y * kBwdTile;
   const int ix = tx0 + (wi % kBwdTile), iy = ty0 + (wi / kBwdTile);
   const bool live = ix < g.nx && iy < g.ny;
@@ -529,11 +567,6 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
   const float Yc = (float)iy + 0.5f - 0.5f * (float)g.ny;
   const float X0 = (float)tx0 + 0.5f - 0.5f * (float)g.nx, Y0 = (float)ty0 + 0.5f - 0.5f * (float)g.ny;
   const float X1 = X0 + (float)(kBwdTile - 1), Y1 = Y0 + (float)(kBwdTile - 1);
-  float4* myL = itL + wi * icap;
-  int4* myM = itM + wi * icap;
-  PixItem* mypix = pix + wi * g.nr_max;
-  const int nviews = subset_views(g, subset);
-  const int nz = g.nz;
   float acc[ZK];
 #pragma unroll
   for (int k = 0; k < ZK; ++k) acc[k] = 0.f;
@@ -588,9 +621,12 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
     if (ok) mypix[__popc(mask & ((1u << lane) - 1u))] = P;
     const int np = __popc(mask);
     __syncwarp();
-    // 3. axial taps per (pair, segment), ordered by tap count: a lane holds up to two items,
-    //    ballots count each tap-count bucket, and the items are written bucket after bucket
-    const int ni = min(np * g.n_seg, bcap);
+    // 3. axial taps per (pair, component), ordered by tap count: a lane holds up to two items,
+    //    ballots count each tap-count bucket, and the items are written bucket after bucket.  The
+    //    components are taken in batches of cpb (one batch unless the bins are mashed).
+    for (int cf = 0; cf < (MASHED ? g.n_comp : 1); cf += cpb) {
+    const int ccount = MASHED ? min(cpb, g.n_comp - cf) : g.n_comp;
+    const int ni = min(np * ccount, bcap);
     float4 Lv2[2];
     int4 Mv2[2];
     int nt2[2] = {0, 0};
@@ -600,17 +636,22 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
       Lv2[h] = make_float4(0.f, 0.f, 0.f, 0.f);
       Mv2[h] = make_int4(0, 0, 0, 0);
       if (it < ni) {
-        const int pi = it / g.n_seg, gi = it - pi * g.n_seg;
+        const int pi = it / ccount, ci = cf + (it - pi * ccount);
         const PixItem Q = mypix[pi];
         float Lk[4] = {0.f, 0.f, 0.f, 0.f};
-        const int j0 = segment_taps<NT>(g, Q.r, gi, Q.I, Lk);
+        const int j0 = segment_taps<NT>(g, Q.r, ci, Q.I, Lk);
         int nt = NT;
         while (nt > 1 && Lk[nt - 1] == 0.f) --nt;
+        const CompDev cd = g.comp[ci];
+        const int gi = cd.seg;
         const SegDev sd = g.seg[gi];
         Lv2[h] = make_float4(Lk[0], Lk[1], Lk[2], Lk[3]);
-        // voxel iz, tap t reads plane q = iz + j0 + t at sw[x + iz + t]; some tap is inside the
-        // segment while -PAD <= iz + j0 < n, and the frame supplies zeros for the others
-        Mv2[h] = make_int4((Q.r - r_min) * p_pad + sd.p0 + (2 * gi + 1) * PAD + j0, j0 + PAD, sd.n + PAD, nt);
+        // voxel iz, tap t reads plane q = iz + j0 + t at sw[x + iz + t]; without mashing some tap is
+        // inside the segment while -PAD <= iz + j0 < n, and the frame supplies zeros for the
+        // others; a mashed component keeps the taps of the planes that include it
+        const int x = (Q.r - r_min) * p_pad + sd.p0 + (2 * gi + 1) * PAD + j0;
+        Mv2[h] = MASHED ? make_int4(x, j0 - cd.qlo, cd.qhi - cd.qlo, cd.smask)
+                        : make_int4(x, j0 + PAD, sd.n + PAD, 0);
         nt2[h] = nt;
       }
     }
@@ -637,10 +678,14 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
       }
       bs[NT] = off;
     }
-    cp_async_commit_wait_all();
-    __syncthreads();
+    if (!MASHED || cf == 0) {
+      cp_async_commit_wait_all();
+      __syncthreads();
+    } else {
+      __syncwarp();
+    }
     // 4. gather: one branch-free loop per tap count
-    if (live) {
+    if (live && !MASHED) {
 #pragma unroll
       for (int b = 0; b < NT; ++b) {
         for (int it = bs[b]; it < bs[b + 1]; ++it) {
@@ -661,7 +706,31 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
           }
         }
       }
+    } else if (live) {
+      // mashed: tap t of voxel iz counts when its plane includes the component
+#pragma unroll
+      for (int b = 0; b < NT; ++b) {
+        for (int it = bs[b]; it < bs[b + 1]; ++it) {
+          const float4 Lv = myL[it];
+          const int4 M = myM[it];
+          const float* src0 = sw + M.x;
+          const float Lt[4] = {Lv.x, Lv.y, Lv.z, Lv.w};
+#pragma unroll
+          for (int k = 0; k < ZK; ++k) {
+            const int iz = lane + 32 * k;
+            float sum = 0.f;
+#pragma unroll
+            for (int t = 0; t <= b; ++t) {
+              const int rel = iz + t + M.y;  // plane - qlo
+              if ((unsigned)rel < (unsigned)M.z && (rel & M.w) == 0) sum = fmaf(Lt[t], src0[iz + t], sum);
+            }
+            acc[k] += sum;
+          }
+        }
+      }
     }
+    if (MASHED) __syncwarp();  // the items are replaced by the next batch's
+    }  // component batches
     __syncthreads();  // the staged rows are replaced by the next view's
   }
   if (!live) return;
@@ -733,10 +802,14 @@ static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cu
   const int rpp = forward_runs_per_part(g);
   const int parts = (g.n_runs + rpp - 1) / rpp;
   const int threads = 32 * ((std::min(rpp, g.n_runs) + kRunsPerWarp - 1) / kRunsPerWarp);
-  const int nseg_tab = g.n_seg;  // a block computes the taps of the segments its runs span
-  const size_t smem = (size_t)2 * kFwdChunk * xs_stride * sizeof(float) +
-                      (size_t)2 * nseg_tab * kFwdChunk * sizeof(TapRecT<NT>) + (size_t)ecap * sizeof(Entry);
-  if (smem > 200 * 1024 || (size_t)kFwdChunk * xs_stride >= ((size_t)1 << kOffBits)) return cudaErrorInvalidValue;
+  // a block computes the taps of the components of the segments its runs span
+  const int ncomp_tab = g.max_part_comps[rpp / kRunsPerWarp];
+  // entries per chunk: 32, fewer when a block holds the taps of many components (mashing)
+  int chunk = kFwdChunk;
+  while (chunk > 4 && (size_t)2 * ncomp_tab * chunk * sizeof(TapRecT<NT>) > 48 * 1024) chunk /= 2;
+  const size_t smem = (size_t)2 * chunk * xs_stride * sizeof(float) +
+                      (size_t)2 * ncomp_tab * chunk * sizeof(TapRecT<NT>) + (size_t)ecap * sizeof(Entry);
+  if (smem > 200 * 1024 || (size_t)chunk * xs_stride >= ((size_t)1 << kOffBits)) return cudaErrorInvalidValue;
   if (MODE == FWD_DATA && !a.sigma) return cudaErrorInvalidValue;
   if ((MODE == FWD_DATA || MODE == FWD_EM) && (!a.b || !a.r || !a.wdy)) return cudaErrorInvalidValue;
   {
@@ -750,7 +823,7 @@ static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cu
                      (size_t)lines * parts > a.ticket_cap))
     return cudaErrorInvalidValue;
   dim3 grid(lines, rsplit, parts);
-  k_forward<NT, MODE><<<grid, threads, smem, s>>>(g, subset, ecap, rsplit, xs_stride, rpp, nseg_tab, a);
+  k_forward<NT, MODE><<<grid, threads, smem, s>>>(g, subset, ecap, rsplit, xs_stride, rpp, ncomp_tab, chunk, a);
   return cudaGetLastError();
 }
 
@@ -782,46 +855,52 @@ static int bwd_rows_per_tile(const DevGeom& g) {
   return (int)floorf(kBwdTile * 1.4143f * g.inv_drp) + 4;
 }
 
-template <int NT, int ZK, int MODE>
+template <int NT, int ZK, int MODE, bool MASHED>
 static cudaError_t bwd_launch(const DevGeom& g, int subset, const BwdArgs& a, cudaStream_t s) {
   // at most floor(sqrt(2) vx / d_radial) + 2 bins of one view cross a pixel
   const int max_pairs = (int)floorf(1.4143f * g.inv_drp) + 2;
-  // items per warp and view (two per lane at most)
-  const int bcap = max_pairs * g.n_seg;
-  if (g.nr_max > 32 || bcap > kBwdMaxItems) return cudaErrorInvalidValue;
+  // components per batch and items per warp and batch (two per lane at most)
+  const int cpb = std::min(g.n_comp, kBwdMaxItems / max_pairs);
+  const int bcap = max_pairs * cpb;
+  if (g.nr_max > 32 || cpb < 1 || bcap > kBwdMaxItems) return cudaErrorInvalidValue;
   const int nr_tile = bwd_rows_per_tile(g);
   const int p_pad = g.P + 2 * (NT - 1) * g.n_seg;  // each segment framed by NT-1 zeros
   const size_t sw_floats = ((size_t)nr_tile * p_pad + 3) & ~(size_t)3;
   const size_t smem = sw_floats * sizeof(float) + (size_t)kBwdWarps * bcap * (sizeof(float4) + sizeof(int4)) +
                       (size_t)kBwdWarps * g.nr_max * sizeof(PixItem) + (size_t)g.P * sizeof(int);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  auto kern = k_backward<NT, ZK, MODE>;
+  auto kern = k_backward<NT, ZK, MODE, MASHED>;
   {
     cudaError_t e = allow_dynamic_smem(kern, smem);
     if (e != cudaSuccess) return e;
   }
   dim3 grid((g.nx + kBwdTile - 1) / kBwdTile, (g.ny + kBwdTile - 1) / kBwdTile);
-  kern<<<grid, kBwdWarps * 32, smem, s>>>(g, subset, nr_tile, p_pad, bcap, a);
+  kern<<<grid, kBwdWarps * 32, smem, s>>>(g, subset, nr_tile, p_pad, bcap, cpb, a);
   return cudaGetLastError();
 }
 
-template <int NT, int MODE>
+template <int NT, int MODE, bool MASHED>
 static cudaError_t bwd_zk(const DevGeom& g, int subset, const BwdArgs& a, cudaStream_t s) {
   const int zk = (g.nz + 31) / 32;
-  if (zk <= 1) return bwd_launch<NT, 1, MODE>(g, subset, a, s);
-  if (zk <= 2) return bwd_launch<NT, 2, MODE>(g, subset, a, s);
-  if (zk <= 4) return bwd_launch<NT, 4, MODE>(g, subset, a, s);
-  if (zk <= 8) return bwd_launch<NT, 8, MODE>(g, subset, a, s);
+  if (zk <= 1) return bwd_launch<NT, 1, MODE, MASHED>(g, subset, a, s);
+  if (zk <= 2) return bwd_launch<NT, 2, MODE, MASHED>(g, subset, a, s);
+  if (zk <= 4) return bwd_launch<NT, 4, MODE, MASHED>(g, subset, a, s);
+  if (zk <= 8) return bwd_launch<NT, 8, MODE, MASHED>(g, subset, a, s);
   return cudaErrorInvalidValue;
+}
+
+template <int NT, int MODE>
+static cudaError_t bwd_mashed(const DevGeom& g, int subset, const BwdArgs& a, cudaStream_t s) {
+  return g.mashed ? bwd_zk<NT, MODE, true>(g, subset, a, s) : bwd_zk<NT, MODE, false>(g, subset, a, s);
 }
 
 template <int MODE>
 static cudaError_t bwd_nt(const DevGeom& g, int subset, const BwdArgs& a, cudaStream_t s) {
   switch (g.taps) {
-    case 1: return bwd_zk<1, MODE>(g, subset, a, s);
-    case 2: return bwd_zk<2, MODE>(g, subset, a, s);
-    case 3: return bwd_zk<3, MODE>(g, subset, a, s);
-    case 4: return bwd_zk<4, MODE>(g, subset, a, s);
+    case 1: return bwd_mashed<1, MODE>(g, subset, a, s);
+    case 2: return bwd_mashed<2, MODE>(g, subset, a, s);
+    case 3: return bwd_mashed<3, MODE>(g, subset, a, s);
+    case 4: return bwd_mashed<4, MODE>(g, subset, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

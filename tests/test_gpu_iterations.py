@@ -209,3 +209,27 @@ def test_scalar_step_sizes_and_iterations_match_oracle(sc):
     st, steps_o = O.spdhg(prob, prior, seq, probs, steps=steps)
     assert rel(g["x"], O.next_primal(st, steps_o)) < 1e-4
     assert rel(g["y"], st.y) < 1e-4
+
+
+@pytest.mark.slow
+def test_full_reconstruction_3d_final_image():
+    """3-D cylindrical scanner 128x128x64, 180 views (21 uneven subsets), TV beta = 0.05, 30 epochs
+    of SPDHG+ from zero on a fixed seeded sequence: final image within 1e-3 of the oracle, the
+    FP64 objective within 1e-5."""
+    import paper_1808_07150_gb300 as pkg
+    sc = synth.config_3d()
+    d, prob = problem(sc, seed=1808, counts=3e7, mult=False)
+    prior = O.Prior("tv", alpha=0.05)
+    probs = O.probabilities(sc.n_subsets, prior)
+    ipe = O.iters_per_epoch(sc.n_subsets, probs)
+    epochs = 30
+    params = pkg.make_params("tv", alpha=0.05, seed=1811, epochs=epochs, objective_every=epochs)
+    x_gpu = np.zeros(sc.image_shape, np.float32)
+    with pkg.Context(sc) as ctx:
+        upload(ctx, d)
+        rep = ctx.spdhg_run(params, x_gpu)
+    seq = np.concatenate([O.sample(1811, ipe, probs, offset=e * ipe) for e in range(epochs)])
+    st, steps = O.spdhg(prob, prior, seq, probs)
+    x_ref = O.next_primal(st, steps)
+    assert rel(x_gpu, x_ref) < 1e-3
+    assert rep["objective"][-1] == pytest.approx(O.objective(prob, prior, x_ref), rel=1e-5)

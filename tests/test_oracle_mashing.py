@@ -82,3 +82,15 @@ def test_oblique_3d_planes():
     # the two oblique pairs (p-1, p+1), (p+1, p-1) exist for the inner planes only
     assert {c[1][1:], c[2][1:]} == {(1, 63, 1)}
     assert abs(c[1][0]) == abs(c[2][0]) == 4.0
+
+
+def test_sampled_mashed_operators_equal_full_ones():
+    sc = synth.tiny_mashed()
+    x = synth.random_image(sc, 3).astype(np.float64)
+    y = synth.random_sinogram(sc, 4).astype(np.float64)
+    np.testing.assert_allclose(O.project_at_bins(sc, x, np.arange(sc.n_bins)), O.project(sc, x).ravel(),
+                               rtol=1e-13, atol=1e-13)
+    for subset in (-1, 1):
+        np.testing.assert_allclose(O.backproject_at_voxels(sc, y, np.arange(sc.n_voxels), subset),
+                                   O.backproject(sc, y * O.subset_mask(sc, subset), subset).ravel(),
+                                   rtol=1e-12, atol=1e-12)
