@@ -287,6 +287,11 @@ enum { SPDHG_TUNE_PRIOR_COLS = 0,   /* prior kernel: voxel columns per block, in
                                        owns two runs of 32 planes, so a line's runs are spread
                                        over ceil(runs / (2 * warps)) blocks */
        SPDHG_TUNE_PRIOR_STAGES = 4, /* prior kernel: rows in its shared-memory pipeline (3 or 4) */
+       SPDHG_TUNE_BWD_TABLE = 5,    /* backprojector of the iterations: 0 reads its (pixel, bin,
+                                       segment) tap items from a table built by spdhg_setup when
+                                       it fits in 40 % of the free device memory (about 7 GB at
+                                       the mMR scale; same results bit for bit); 1 computes them in
+                                       the kernel */
        SPDHG_TUNE_KNOBS = 8 };
 
 /* Sets one launch-shape knob of the context (value 0: default).  Out-of-range values are rejected

@@ -266,6 +266,10 @@ int spdhg::enqueue_block(spdhg_ctx* ctx, int i, cudaStream_t s) {
     ba.z = ctx->z;
     ba.T = ctx->T;
     ba.inv_p = inv_p;
+    if (ctx->bwd_table == 1) {
+      ba.items = ctx->bwd_items;
+      ba.hdr = ctx->bwd_hdr;
+    }
     {
       ProfScope ps(ctx, SPDHG_KERNEL_BACKWARD, s);
       CK(launch_backward(ctx->dg, i, BWD_UPDATE, ba, s));
@@ -350,6 +354,88 @@ cudaError_t spdhg::allow_dynamic_smem_fn(const void* kern, size_t smem) {
     it = limit.emplace(std::make_pair(dev, kern), lim).first;
   }
   return smem <= (size_t)it->second ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Builds the backprojector's tap-item table once per context (geometry only): counted, scanned per
+// view, then filled by the same code the kernel runs.  Not built when the geometry does not admit
+// it, when the knob switches it off, or when it would take more than 40 % of the free device
+// memory (the kernel then computes the items itself; the results are the same bits either way).
+static int build_bwd_table(spdhg_ctx* ctx, cudaStream_t s) {
+  if (ctx->bwd_table >= 0) return SPDHG_OK;
+  ctx->bwd_table = 0;
+  const DevGeom& g = ctx->dg;
+  if (g.tune[SPDHG_TUNE_BWD_TABLE] == 1 || !backward_table_possible(g)) return SPDHG_OK;
+  const size_t cols = (size_t)((g.nx + 3) / 4) * ((g.ny + 3) / 4) * 16;
+  const size_t V = (size_t)g.V;
+  unsigned char* cnt = nullptr;
+  unsigned *bad = nullptr, *starts = nullptr, *totals = nullptr;
+  int status = SPDHG_OK;
+  auto release = [&]() {
+    if (cnt) cudaFree(cnt);
+    if (bad) cudaFree(bad);
+    if (starts) cudaFree(starts);
+    if (totals) cudaFree(totals);
+  };
+  if (cudaMalloc(&cnt, V * cols) != cudaSuccess || cudaMalloc(&bad, sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&starts, V * cols * sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc(&totals, V * sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    release();
+    return SPDHG_OK;  // no room for the table: the kernel computes the items
+  }
+  cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = backward_table_count(g, cnt, bad, s);
+  if (e == cudaSuccess) e = backward_table_starts(g, cnt, starts, totals, s);
+  std::vector<unsigned> tot(V);
+  unsigned hbad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tot.data(), totals, V * sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    release();
+    return fail(ctx, SPDHG_ERR_CUDA, std::string("backprojector table: ") + cudaGetErrorString(e));
+  }
+  std::vector<unsigned> base(V);
+  uint64_t total = 0;
+  for (size_t v = 0; v < V; ++v) {
+    base[v] = (unsigned)total;
+    total += tot[v];
+  }
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  const size_t need = (size_t)total * sizeof(float4) + V * cols * sizeof(int2);
+  if (hbad || total >= (1ull << 32) || need > free_b / 10 * 4) {
+    release();
+    return SPDHG_OK;
+  }
+  if (cudaMalloc(&ctx->bwd_items, (size_t)total * sizeof(float4) + 16) != cudaSuccess ||
+      cudaMalloc(&ctx->bwd_hdr, V * cols * sizeof(int2)) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->bwd_items) cudaFree(ctx->bwd_items);
+    if (ctx->bwd_hdr) cudaFree(ctx->bwd_hdr);
+    ctx->bwd_items = nullptr;
+    ctx->bwd_hdr = nullptr;
+    release();
+    return SPDHG_OK;
+  }
+  e = cudaMemcpyAsync(totals, base.data(), V * sizeof(unsigned), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = backward_table_fill(g, starts, totals, ctx->bwd_items, ctx->bwd_hdr, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  release();
+  if (e != cudaSuccess) return fail(ctx, SPDHG_ERR_CUDA, std::string("backprojector table: ") + cudaGetErrorString(e));
+  ctx->bwd_table = 1;
+  ++ctx->graph_gen;
+  return status;
+}
+
+// Drops the table (a knob changed); the next spdhg_setup decides again.
+static void drop_bwd_table(spdhg_ctx* ctx) {
+  if (ctx->bwd_items) cudaFree(ctx->bwd_items);
+  if (ctx->bwd_hdr) cudaFree(ctx->bwd_hdr);
+  ctx->bwd_items = nullptr;
+  ctx->bwd_hdr = nullptr;
+  ctx->bwd_table = -1;
+  ++ctx->graph_gen;
 }
 
 int spdhg::forward_scratch(spdhg_ctx* ctx, int subset, FwdArgs& a, cudaStream_t s) {
@@ -619,7 +705,7 @@ void spdhg_destroy(spdhg_ctx* ctx) {
   if (!ctx) return;
   void* ptrs[] = {ctx->d_view, ctx->d_view_inv, ctx->d_rad, ctx->d_rs, ctx->d_runs, ctx->d_seg, ctx->d_comp, ctx->d_plane_seg, ctx->b, ctx->r, ctx->mult, ctx->side,
                   ctx->x[0], ctx->x[1], ctx->z, ctx->T, ctx->y, ctx->sigma, ctx->wdy, ctx->q[0], ctx->q[1],
-                  ctx->w[0], ctx->w[1], ctx->zw, ctx->q2[0], ctx->q2[1], ctx->tgv_b, ctx->tmp_sino, ctx->tmp_img, ctx->tmp_img2, ctx->em_sens, ctx->fwd_part, ctx->fwd_tickets,
+                  ctx->w[0], ctx->w[1], ctx->zw, ctx->q2[0], ctx->q2[1], ctx->tgv_b, ctx->tmp_sino, ctx->tmp_img, ctx->tmp_img2, ctx->em_sens, ctx->bwd_items, ctx->bwd_hdr, ctx->fwd_part, ctx->fwd_tickets,
                   ctx->red, ctx->red_out};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -922,6 +1008,7 @@ int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int
     CK(cudaMemsetAsync(ctx->q2[0], 0, 6 * N * sizeof(float), s));
   }
   ctx->iterations = 0;
+  if (int st = build_bwd_table(ctx, s)) return st;
   ctx->is_setup = true;
   return SPDHG_OK;
 }
@@ -1313,6 +1400,10 @@ int spdhg_tune(spdhg_ctx* ctx, int knob, int value) {
       break;
     case SPDHG_TUNE_FWD_SPLIT:
       if (value > 16) return fail(ctx, SPDHG_ERR_ARG, "forward split out of range");
+      break;
+    case SPDHG_TUNE_BWD_TABLE:
+      if (value > 1) return fail(ctx, SPDHG_ERR_ARG, "backprojector table knob must be 0 or 1");
+      if (ctx->dg.tune[knob] != value) drop_bwd_table(ctx);
       break;
     case SPDHG_TUNE_FWD_WARPS:
       if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)

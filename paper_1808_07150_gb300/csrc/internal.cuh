@@ -132,7 +132,25 @@ struct BwdArgs {
   float* x;              // BWD_UPDATE, BWD_EM
   float* z;
   float inv_p;
+  // BWD_UPDATE: the tap items of every (view, tile, column), built once (null: computed in the
+  // kernel); see backward_table_count / _fill
+  const float4* items;
+  const int2* hdr;
 };
+
+// Tap-item table of the backprojector: for every view, 4 x 4 tile and column the (pair, segment)
+// items the kernel would compute, in its order.  Items are float4 (L0, L1, L2, packed): packed =
+// shared offset (16 bits) | (j0 + taps - 1 + 256) << 16 (9 bits) | segment << 25 (7 bits).  Header
+// per column: (first item, n1 | (n1 + n2) << 8 | n << 16) with n_k the items of k taps.
+// Pass 0 counts the items per column into `cnt` (bytes) and flags an item that does not fit the
+// packing in *bad; pass 1 fills the items and headers from the per-column starts.
+cudaError_t backward_table_count(const DevGeom& g, unsigned char* cnt, unsigned* bad, cudaStream_t s);
+cudaError_t backward_table_starts(const DevGeom& g, const unsigned char* cnt, unsigned* starts,
+                                  unsigned* view_totals, cudaStream_t s);
+cudaError_t backward_table_fill(const DevGeom& g, const unsigned* starts, const unsigned* view_base,
+                                float4* items, int2* hdr, cudaStream_t s);
+// whether the geometry admits the table (unmashed, at most 3 taps, packing limits)
+bool backward_table_possible(const DevGeom& g);
 
 cudaError_t launch_forward(const DevGeom& g, int subset, int mode, const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_backward(const DevGeom& g, int subset, int mode, const BwdArgs& a, cudaStream_t s);
@@ -259,6 +277,9 @@ struct spdhg_ctx {
   float* tmp_img = nullptr;    // N floats (objective of a host image, Psi(0), x* of spdhg_psnr)
   float* tmp_img2 = nullptr;   // N floats (x of spdhg_psnr from the host)
   float* em_sens = nullptr;    // OSEM / MLEM sensitivity images P_i^T 1 (m x N, or N for MLEM)
+  float4* bwd_items = nullptr; // backprojector tap-item table (see backward_table_count / _fill)
+  int2* bwd_hdr = nullptr;
+  int bwd_table = -1;          // -1 not tried, 0 not built (does not fit / not possible), 1 built
   int em_sens_kind = -1;       // which set em_sens holds: 0 OSEM, 1 MLEM, -1 none (reset by set_data)
   float* fwd_part = nullptr;   // forward row-split partial sums (2 x fwd_part_cap floats)
   unsigned* fwd_tickets = nullptr;

@@ -543,7 +543,7 @@ constexpr int kBwdMaxItems = 64;         // (pair, segment) items per column and
 // compute the axial taps of every (pair, segment) item, and then gather along contiguous plane
 // runs from shared memory, lane = iz mod 32, ZK voxels per lane.  Up to 128 slices (ZK <= 4) four
 // blocks share an SM (32 registers per thread); with eight accumulators per lane, three.
-template <int NT, int ZK, int MODE, bool MASHED>
+template <int NT, int ZK, int MODE, bool MASHED, bool TAB>
 __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(DevGeom g, int subset, int nr_tile, int p_pad,
                                                              int bcap, int cpb, BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -602,10 +602,27 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
         for (int rr = 0; rr < nr; ++rr) cp_async4(sw + rr * p_pad + dst, src + rr * g.P + p);
       }
     }
+    int bs[5] = {0, 0, 0, 0, 0};  // bucket b (items with b + 1 taps) spans [bs[b], bs[b + 1])
+    if constexpr (TAB) {
+      // 2-3. this column's items, in the order the code below computes them, from the table
+      const int2 h = a.hdr[((size_t)v * gridDim.x * gridDim.y + (size_t)blockIdx.y * gridDim.x + blockIdx.x) *
+                               kBwdWarps + wi];
+      const int n = h.y >> 16;
+      bs[1] = h.y & 0xFF;
+      if (NT > 2) bs[2] = (h.y >> 8) & 0xFF;
+      bs[NT] = n;
+      for (int it = lane; it < n; it += 32) {
+        const float4 e = a.items[(size_t)(unsigned)h.x + it];
+        const unsigned pk = __float_as_uint(e.w);
+        const int gi = (int)(pk >> 25);
+        myL[it] = make_float4(e.x, e.y, e.z, 0.f);
+        myM[it] = make_int4((int)(pk & 0xFFFFu), (int)((pk >> 16) & 0x1FFu) - 256, g.seg[gi].n + PAD, 0);
+      }
+    }
     // 2. footprint pairs of this warp's column (overlaps the copy)
     PixItem P;
     bool ok = false;
-    if (live && lane < g.nr_max) {
+    if (!TAB && live && lane < g.nr_max) {
       const float sc = Xc * cs.x + Yc * cs.z;
       const int rlo = (int)ceilf((sc - hw) * g.inv_drp + g.half_R) - 1;
       const int rhi = (int)floorf((sc + hw) * g.inv_drp + g.half_R) + 1;
@@ -618,7 +635,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
       }
     }
     const unsigned mask = __ballot_sync(0xffffffffu, ok);
-    if (ok) mypix[__popc(mask & ((1u << lane) - 1u))] = P;
+    if (!TAB && ok) mypix[__popc(mask & ((1u << lane) - 1u))] = P;
     const int np = __popc(mask);
     __syncwarp();
     // 3. axial taps per (pair, component), ordered by tap count: a lane holds up to two items,
@@ -626,7 +643,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
     //    components are taken in batches of cpb (one batch unless the bins are mashed).
     for (int cf = 0; cf < (MASHED ? g.n_comp : 1); cf += cpb) {
     const int ccount = MASHED ? min(cpb, g.n_comp - cf) : g.n_comp;
-    const int ni = min(np * ccount, bcap);
+    const int ni = TAB ? 0 : min(np * ccount, bcap);
     float4 Lv2[2];
     int4 Mv2[2];
     int nt2[2] = {0, 0};
@@ -655,8 +672,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
         nt2[h] = nt;
       }
     }
-    int bs[5] = {0, 0, 0, 0, 0};  // bucket b (items with b + 1 taps) spans [bs[b], bs[b + 1])
-    {
+    if (!TAB) {
       int off = 0;
 #pragma unroll
       for (int b = 0; b < NT; ++b) {
@@ -755,6 +771,170 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
       a.x[idx] = prox_nonneg(a.x[idx] - a.T[idx] * fmaf(acc[k], a.inv_p, zn));
     }
   }
+}
+
+// ---------------------------------------------------------------------------------------
+// tap-item table of the backprojector: the (pair, segment) items of every view, tile and column,
+// computed once by the code the kernel runs and read back by k_backward_tab
+// ---------------------------------------------------------------------------------------
+
+constexpr int kTabMaxPairs = 16;  // candidate radial bins per column and view (nr_max <= 16)
+
+template <int NT, int PASS>
+__global__ void __launch_bounds__(kBwdWarps * 32) k_bwd_items(DevGeom g, int nr_tile, int p_pad, int bcap,
+                                                           unsigned char* cnt, unsigned* bad, const unsigned* starts,
+                                                           const unsigned* view_base, float4* items, int2* hdr) {
+  __shared__ PixItem pix[kBwdWarps][kTabMaxPairs];
+  constexpr int PAD = NT - 1;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const int tx0 = blockIdx.x * kBwdTile, ty0 = blockIdx.y * kBwdTile;
+  const int ix = tx0 + (wi % kBwdTile), iy = ty0 + (wi / kBwdTile);
+  const bool live = ix < g.nx && iy < g.ny;
+  const float Xc = (float)ix + 0.5f - 0.5f * (float)g.nx;
+  const float Yc = (float)iy + 0.5f - 0.5f * (float)g.ny;
+  const float X0 = (float)tx0 + 0.5f - 0.5f * (float)g.nx, Y0 = (float)ty0 + 0.5f - 0.5f * (float)g.ny;
+  const float X1 = X0 + (float)(kBwdTile - 1), Y1 = Y0 + (float)(kBwdTile - 1);
+  const int v = blockIdx.z;
+  const size_t col = ((size_t)v * gridDim.x * gridDim.y + (size_t)blockIdx.y * gridDim.x + blockIdx.x) * kBwdWarps + wi;
+  PixItem* mypix = pix[wi];
+  // the same arithmetic as k_backward for view v
+  const float4 cs = g.view[v];
+  const float hw = 0.5f * (fabsf(cs.x) + fabsf(cs.z));
+  const float s00 = X0 * cs.x + Y0 * cs.z, s01 = X0 * cs.x + Y1 * cs.z;
+  const float s10 = X1 * cs.x + Y0 * cs.z, s11 = X1 * cs.x + Y1 * cs.z;
+  const float smin = fminf(fminf(s00, s01), fminf(s10, s11)), smax = fmaxf(fmaxf(s00, s01), fmaxf(s10, s11));
+  const int r_min = max(0, (int)ceilf((smin - hw) * g.inv_drp + g.half_R) - 1);
+  const int r_max = min(g.R - 1, min(r_min + nr_tile - 1, (int)floorf((smax + hw) * g.inv_drp + g.half_R) + 1));
+  PixItem P;
+  bool ok = false;
+  if (live && lane < g.nr_max) {
+    const float sc = Xc * cs.x + Yc * cs.z;
+    const int rlo = (int)ceilf((sc - hw) * g.inv_drp + g.half_R) - 1;
+    const int rhi = (int)floorf((sc + hw) * g.inv_drp + g.half_R) + 1;
+    const int r = rlo + lane;
+    if (r >= r_min && r <= r_max && r <= rhi) {
+      const Line L = make_line(g, v, r);
+      ok = pixel_interval(g, L, ix, iy, P.I);
+      P.l = v;
+      P.r = r;
+    }
+  }
+  const unsigned mask = __ballot_sync(0xffffffffu, ok);
+  if (ok) mypix[__popc(mask & ((1u << lane) - 1u))] = P;
+  const int np = __popc(mask);
+  __syncwarp();
+  const int ccount = g.n_comp;
+  const int ni = min(np * ccount, bcap);
+  float4 It[2];
+  int nt2[2] = {0, 0};
+  bool misfit = false;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int it = lane + 32 * h;
+    It[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (it < ni) {
+      const int pi = it / ccount, ci = it - pi * ccount;
+      const PixItem Q = mypix[pi];
+      float Lk[4] = {0.f, 0.f, 0.f, 0.f};
+      const int j0 = segment_taps<NT>(g, Q.r, ci, Q.I, Lk);
+      int nt = NT;
+      while (nt > 1 && Lk[nt - 1] == 0.f) --nt;
+      const int gi = g.comp[ci].seg;
+      const SegDev sd = g.seg[gi];
+      const int x = (Q.r - r_min) * p_pad + sd.p0 + (2 * gi + 1) * PAD + j0;
+      const int jp = j0 + PAD + 256;
+      misfit = misfit || x < 0 || x >= 65536 || jp < 0 || jp >= 512 || gi >= 128;
+      const unsigned packed = ((unsigned)x & 0xFFFFu) | (((unsigned)jp & 0x1FFu) << 16) | ((unsigned)gi << 25);
+      It[h] = make_float4(Lk[0], Lk[1], Lk[2], __uint_as_float(packed));
+      nt2[h] = nt;
+    }
+  }
+  int bs[4] = {0, 0, 0, 0};
+  unsigned base = 0;
+  if (PASS == 1) base = view_base[v] + starts[col];
+  {
+    int off = 0;
+#pragma unroll
+    for (int b = 0; b < NT; ++b) {
+      const unsigned m0 = __ballot_sync(0xffffffffu, nt2[0] == b + 1);
+      const unsigned m1 = __ballot_sync(0xffffffffu, nt2[1] == b + 1);
+      const unsigned below = (1u << lane) - 1u;
+      if (PASS == 1) {
+        if (nt2[0] == b + 1) items[base + off + __popc(m0 & below)] = It[0];
+        if (nt2[1] == b + 1) items[base + off + __popc(m0) + __popc(m1 & below)] = It[1];
+      }
+      off += __popc(m0) + __popc(m1);
+      bs[b + 1] = off;
+    }
+  }
+  if (PASS == 0) {
+    if (__any_sync(0xffffffffu, misfit) && lane == 0) atomicOr(bad, 1u);
+    if (lane == 0) cnt[col] = (unsigned char)bs[NT];
+  } else if (lane == 0) {
+    const int n1 = bs[1], n12 = NT > 2 ? bs[2] : bs[NT], n = bs[NT];
+    hdr[col] = make_int2((int)base, n1 | (n12 << 8) | (n << 16));
+  }
+}
+
+// per view: exclusive prefix sums of the columns' item counts, and the view's total
+__global__ void __launch_bounds__(1024) k_bwd_table_scan(const unsigned char* cnt, size_t cols_per_view,
+                                                         unsigned* starts, unsigned* totals) {
+  __shared__ int scratch[33];
+  const size_t v = blockIdx.x;
+  const unsigned char* c = cnt + v * cols_per_view;
+  unsigned* st = starts + v * cols_per_view;
+  const size_t per = (cols_per_view + blockDim.x - 1) / blockDim.x;
+  const size_t lo = min(cols_per_view, threadIdx.x * per), hi = min(cols_per_view, lo + per);
+  int sum = 0;
+  for (size_t k = lo; k < hi; ++k) sum += c[k];
+  int total;
+  int run = block_exclusive_scan(sum, scratch, &total);
+  for (size_t k = lo; k < hi; ++k) {
+    st[k] = (unsigned)run;
+    run += c[k];
+  }
+  if (threadIdx.x == 0) totals[v] = (unsigned)total;
+}
+
+bool backward_table_possible(const DevGeom& g) {
+  const int max_pairs = (int)floorf(1.4143f * g.inv_drp) + 2;
+  return !g.mashed && !g.bins && g.taps <= 3 && g.nr_max <= kTabMaxPairs && max_pairs * g.n_comp <= kBwdMaxItems;
+}
+
+static int bwd_rows_per_tile(const DevGeom& g);
+
+template <int PASS>
+static cudaError_t table_pass(const DevGeom& g, unsigned char* cnt, unsigned* bad, const unsigned* starts,
+                              const unsigned* view_base, float4* items, int2* hdr, cudaStream_t s) {
+  if (!backward_table_possible(g)) return cudaErrorInvalidValue;
+  const int max_pairs = (int)floorf(1.4143f * g.inv_drp) + 2;
+  const int bcap = max_pairs * g.n_comp;
+  const int nr_tile = bwd_rows_per_tile(g);
+  const int NT = g.taps;
+  const int p_pad = g.P + 2 * (NT - 1) * g.n_seg;
+  dim3 grid((g.nx + kBwdTile - 1) / kBwdTile, (g.ny + kBwdTile - 1) / kBwdTile, g.V);
+  switch (NT) {
+    case 1: k_bwd_items<1, PASS><<<grid, kBwdWarps * 32, 0, s>>>(g, nr_tile, p_pad, bcap, cnt, bad, starts, view_base, items, hdr); break;
+    case 2: k_bwd_items<2, PASS><<<grid, kBwdWarps * 32, 0, s>>>(g, nr_tile, p_pad, bcap, cnt, bad, starts, view_base, items, hdr); break;
+    default: k_bwd_items<3, PASS><<<grid, kBwdWarps * 32, 0, s>>>(g, nr_tile, p_pad, bcap, cnt, bad, starts, view_base, items, hdr); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t backward_table_count(const DevGeom& g, unsigned char* cnt, unsigned* bad, cudaStream_t s) {
+  return table_pass<0>(g, cnt, bad, nullptr, nullptr, nullptr, nullptr, s);
+}
+
+cudaError_t backward_table_starts(const DevGeom& g, const unsigned char* cnt, unsigned* starts,
+                                  unsigned* view_totals, cudaStream_t s) {
+  const size_t cols = (size_t)((g.nx + kBwdTile - 1) / kBwdTile) * ((g.ny + kBwdTile - 1) / kBwdTile) * kBwdWarps;
+  k_bwd_table_scan<<<g.V, 1024, 0, s>>>(cnt, cols, starts, view_totals);
+  return cudaGetLastError();
+}
+
+cudaError_t backward_table_fill(const DevGeom& g, const unsigned* starts, const unsigned* view_base,
+                                float4* items, int2* hdr, cudaStream_t s) {
+  return table_pass<1>(g, nullptr, nullptr, starts, view_base, items, hdr, s);
 }
 
 __global__ void k_gather_subset(DevGeom g, int subset, const float* __restrict__ y,
@@ -869,7 +1049,9 @@ static cudaError_t bwd_launch(const DevGeom& g, int subset, const BwdArgs& a, cu
   const size_t smem = sw_floats * sizeof(float) + (size_t)kBwdWarps * bcap * (sizeof(float4) + sizeof(int4)) +
                       (size_t)kBwdWarps * g.nr_max * sizeof(PixItem) + (size_t)g.P * sizeof(int);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  auto kern = k_backward<NT, ZK, MODE, MASHED>;
+  auto kern = a.items ? k_backward<NT, ZK, MODE, MASHED, (MODE == BWD_UPDATE && !MASHED && NT <= 3)>
+                      : k_backward<NT, ZK, MODE, MASHED, false>;
+  if (a.items && (MODE != BWD_UPDATE || MASHED || NT > 3)) return cudaErrorInvalidValue;
   {
     cudaError_t e = allow_dynamic_smem(kern, smem);
     if (e != cudaSuccess) return e;

@@ -176,3 +176,31 @@ def test_autotune_keeps_state_and_parity(kind):
         xg = host(x)
     st, steps = O.spdhg(prob, prior, seq, probs)
     assert rel(xg, O.next_primal(st, steps)) < 1e-4
+
+
+@pytest.mark.parametrize("sc", [synth.tiny_3d(steep=True), synth.config_2d(), synth.config_3d_small()],
+                         ids=lambda s: s.name)
+def test_backprojector_item_table_is_bit_identical(sc):
+    """The backprojector's tap items read from the table spdhg_setup builds give the same bits as
+    the items the kernel computes itself (knob bwd_table = 1)."""
+    import paper_1808_07150_gb300 as pkg
+    import torch
+    d, prob = problem(sc)
+    probs = O.probabilities(sc.n_subsets, _prior("tv"))
+    seq = O.sample(77, 40, probs)
+    out = []
+    for off in (0, 1):
+        with pkg.Context(sc) as ctx:
+            upload(ctx, d)
+            ctx.spdhg_tune("bwd_table", off)
+            ctx.spdhg_setup(_params(pkg, "tv", 1, False))
+            ctx.spdhg_iterate(seq)
+            st = {}
+            for k, n in (("x", sc.n_voxels), ("z", sc.n_voxels), ("y", sc.n_bins), ("T", sc.n_voxels)):
+                t = torch.zeros(n, device="cuda")
+                ctx.spdhg_get(k, t)
+                st[k] = t
+            torch.cuda.synchronize()
+            out.append({k: host(v) for k, v in st.items()})
+    for k in out[0]:
+        np.testing.assert_array_equal(out[0][k], out[1][k], err_msg=k)
