@@ -292,6 +292,10 @@ enum { SPDHG_TUNE_PRIOR_COLS = 0,   /* prior kernel: voxel columns per block, in
                                        it fits in 40 % of the free device memory (about 7 GB at
                                        the mMR scale; same results bit for bit); 1 computes them in
                                        the kernel */
+       SPDHG_TUNE_FWD_GROUPS = 6,   /* forward projector: warps that share each plane run, each
+                                       taking every k-th pixel entry of the line (1 .. 8; their
+                                       partial sums are added in a fixed order); 0 = enough for
+                                       four warps per block when a line has few plane runs */
        SPDHG_TUNE_KNOBS = 8 };
 
 /* Sets one launch-shape knob of the context (value 0: default).  Out-of-range values are rejected

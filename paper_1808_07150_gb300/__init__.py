@@ -186,8 +186,8 @@ class Context:
         return {k: out[i] for k, i in _capi.TUNE.items()}
 
     def spdhg_tune(self, knob, value):
-        """Sets a launch-shape knob ('prior_cols', 'prior_ychunk', 'fwd_split', 'fwd_warps', 'prior_stages');
-        0 = default."""
+        """Sets a launch-shape knob ('prior_cols', 'prior_ychunk', 'fwd_split', 'fwd_warps', 'prior_stages',
+        'bwd_table', 'fwd_groups'); 0 = default."""
         code = _capi.TUNE[knob] if isinstance(knob, str) else int(knob)
         self._check(_capi.lib().spdhg_tune(self.h, code, int(value)))
 

@@ -30,7 +30,8 @@ _EXPORTS = [
     "unet_gemm", "unet_device_error", "unet_create", "unet_destroy", "unet_last_error", "unet_num_params",
     "unet_set_params", "unet_init", "unet_get_params", "unet_get_grads", "unet_forward", "unet_backward", "unet_adam_step",
 ]
-TUNE = {"prior_cols": 0, "prior_ychunk": 1, "fwd_split": 2, "fwd_warps": 3, "prior_stages": 4, "bwd_table": 5}
+TUNE = {"prior_cols": 0, "prior_ychunk": 1, "fwd_split": 2, "fwd_warps": 3, "prior_stages": 4, "bwd_table": 5,
+        "fwd_groups": 6}
 TUNE_KNOBS = 8
 KERNELS = ["forward", "backward", "prior", "tgv", "w_step"]
 

@@ -1405,6 +1405,9 @@ int spdhg_tune(spdhg_ctx* ctx, int knob, int value) {
       if (value > 1) return fail(ctx, SPDHG_ERR_ARG, "backprojector table knob must be 0 or 1");
       if (ctx->dg.tune[knob] != value) drop_bwd_table(ctx);
       break;
+    case SPDHG_TUNE_FWD_GROUPS:
+      if (value > 8) return fail(ctx, SPDHG_ERR_ARG, "forward entry groups must be 1 .. 8");
+      break;
     case SPDHG_TUNE_FWD_WARPS:
       if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
         return fail(ctx, SPDHG_ERR_ARG, "forward warps must be 1, 2, 4, 8 or 16");

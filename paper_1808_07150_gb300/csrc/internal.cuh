@@ -123,6 +123,7 @@ struct FwdArgs {
 int forward_split(const DevGeom& g, int subset);
 // plane parts per LOR line (blocks that share the rows of a line, each with its own planes)
 int forward_parts(const DevGeom& g);
+int forward_entry_groups(const DevGeom& g);
 
 struct BwdArgs {
   const float* w;        // subset-local sinogram (mult already applied)

@@ -202,6 +202,9 @@ __device__ __forceinline__ int row_entries(const DevGeom& g, const Line& L, bool
 
 constexpr int kFwdChunk = 32;  // pixel entries per double-buffered chunk
 constexpr int kRunsPerWarp = 2;  // 32-plane runs per warp (lane = plane within a run)
+// Entry groups: when a line has few plane runs (a shallow volume), several warps share each run,
+// each taking every egroups-th pixel entry, and their partial sums are added in group order.
+constexpr int kFwdMaxGroupWarps = 7;  // warps of groups 1.. (their sums are staged in shared)
 
 // Block-wide exclusive prefix sum of one int per thread (blockDim <= 1024); returns the
 // exclusive prefix and writes the total to *total.  Uses `scratch` (>= 33 ints of shared).
@@ -278,11 +281,14 @@ __device__ __forceinline__ float taps_dot(const Rec& t, int nt, const float* xp,
 // of every plane of the segments (the axial bound of the geometry, so no plane needs a range
 // test), and its axial taps computed while chunk c is accumulated.  When both runs of a warp lie
 // in one segment, one tap record serves both and a packed FP32 FMA accumulates the two planes.
+// When a line has few runs, egroups warps share each pair of runs, warp group k taking the
+// entries k, k + egroups, ... of every chunk; group 0 adds the other groups' sums in group order.
 // When several row parts share a line, each writes partial plane sums and the last one to finish
 // reduces them in a fixed order.
-template <int NT, int MODE>
+template <int NT, int MODE, bool GROUPS>
 __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap, int rsplit, int xs_stride,
-                                                 int runs_per_part, int ncomp_tab, int chunk, FwdArgs a) {
+                                                 int runs_per_part, int ncomp_tab, int chunk, int egroups_arg,
+                                                 FwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int scan_scratch[33];
   const int FL = g.fz_lo;
@@ -290,6 +296,7 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
   using Rec = TapRecT<NT>;
   Rec* taps = reinterpret_cast<Rec*>(xs + 2 * chunk * xs_stride);              // [2][ncomp_tab][chunk]
   Entry* ent = reinterpret_cast<Entry*>(taps + 2 * ncomp_tab * chunk);         // [ecap]
+  float* group_acc = reinterpret_cast<float*>(ent + ecap);  // [egroups - 1][nrw][2][32] partial sums
   const int nz = g.nz;
 
   const int line = blockIdx.x, rpart = blockIdx.y, ppart = blockIdx.z;
@@ -297,8 +304,11 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
   const int v = subset_view(g, subset, l);
   const Line L = make_line(g, v, r);
 
-  // this thread's planes: lane of runs rf + 2w and rf + 2w + 1 of the plane part
+  // this thread's planes: lane of runs rf + 2w and rf + 2w + 1 of the plane part, w = wi mod
+  // nrw; warp wi takes every egroups-th pixel entry from entry wi / nrw on
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int egroups = GROUPS ? egroups_arg : 1;
+  const int nrw = GROUPS ? nw / egroups : nw, rw = GROUPS ? wi % nrw : wi, eg = GROUPS ? wi / nrw : 0;
   const int rfirst = ppart * runs_per_part;
   const int rlast = min(g.n_runs, rfirst + runs_per_part) - 1;
   const int g_lo = g.runs[rfirst].x, g_hi = g.runs[rlast].x;
@@ -309,7 +319,7 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
   bool valid_[kRunsPerWarp];
 #pragma unroll
   for (int k = 0; k < kRunsPerWarp; ++k) {
-    const int run = rfirst + kRunsPerWarp * wi + k;
+    const int run = rfirst + kRunsPerWarp * rw + k;
     const int2 ru = g.runs[min(run, rlast)];
     const SegDev sd = g.seg[ru.x];
     gs_[k] = ru.x;
@@ -399,6 +409,7 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
     __syncthreads();
     const int buf = c & 1;
     const int ne = min(chunk, n_ent - c * chunk);
+    const int nk = !GROUPS ? ne : (ne > eg ? (ne - eg + egroups - 1) / egroups : 0);  // entries eg + k egroups
     const float* xb = xs + buf * chunk * xs_stride;
     if (g.mashed) {
       // each plane sums the components of its segment it includes (exact mashing)
@@ -411,8 +422,8 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
           const bool in = (incl_[k] >> ci) & 1u;
           const Rec* tc = trk + ci * chunk;
           float sc = 0.f;
-          for (int e = 0; e < ne; ++e) {
-            const Rec t = tc[e];
+          for (int kk = 0; kk < nk; ++kk) {
+            const Rec t = tc[eg + kk * egroups];
             sc = taps_dot<NT>(t, NT > 1 ? (t.off >> kOffBits) : 1, xb + (t.off & kOffMask) + qr_[k], sc);
           }
           sk += in ? sc : 0.f;
@@ -426,8 +437,8 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
     if (same) {
       float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll 1
-      for (int e = 0; e < ne; ++e) {
-        const Rec t = tr0[e];
+      for (int k = 0; k < nk; ++k) {
+        const Rec t = tr0[eg + k * egroups];
         const int off = t.off & kOffMask, nt = NT > 1 ? (t.off >> kOffBits) : 1;
         const float* xa = xb + off + qr_[0];
         const float* xc = xb + off + qr_[1];
@@ -447,7 +458,8 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
     } else {
       const Rec* tr1 = taps + buf * ncomp_tab * chunk + (gs_[1] - g_lo) * chunk;
       float s0 = 0.f, s1 = 0.f;
-      for (int e = 0; e < ne; ++e) {
+      for (int k = 0; k < nk; ++k) {
+        const int e = eg + k * egroups;
         const Rec t0 = tr0[e], t1 = tr1[e];
         s0 = taps_dot<NT>(t0, NT > 1 ? (t0.off >> kOffBits) : 1, xb + (t0.off & kOffMask) + qr_[0], s0);
         s1 = taps_dot<NT>(t1, NT > 1 ? (t1.off >> kOffBits) : 1, xb + (t1.off & kOffMask) + qr_[1], s1);
@@ -456,6 +468,24 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
       acc[1] += s1;
     }
     __syncthreads();
+  }
+
+  if (GROUPS) {
+    // entry groups 1.. hand their partial sums to group 0, which adds them in group order
+    if (eg > 0) {
+#pragma unroll
+      for (int k = 0; k < kRunsPerWarp; ++k) group_acc[(((eg - 1) * nrw + rw) * kRunsPerWarp + k) * 32 + lane] = acc[k];
+    }
+    __syncthreads();
+    if (eg == 0) {
+      for (int q = 1; q < egroups; ++q) {
+#pragma unroll
+        for (int k = 0; k < kRunsPerWarp; ++k) acc[k] += group_acc[(((q - 1) * nrw + rw) * kRunsPerWarp + k) * 32 + lane];
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kRunsPerWarp; ++k) valid_[k] = false;  // group 0 writes the planes
+    }
   }
 
   if (rsplit > 1) {
@@ -974,6 +1004,15 @@ int forward_parts(const DevGeom& g) {
   return (g.n_runs + rpp - 1) / rpp;
 }
 
+// entry groups per block: at least four warps per block when the runs of a part need fewer
+int forward_entry_groups(const DevGeom& g) {
+  const int rpp = forward_runs_per_part(g);
+  const int nrw = (std::min(rpp, g.n_runs) + kRunsPerWarp - 1) / kRunsPerWarp;
+  int eg = g.tune[SPDHG_TUNE_FWD_GROUPS] ? g.tune[SPDHG_TUNE_FWD_GROUPS] : std::max(1, 4 / nrw);
+  while (eg > 1 && ((eg - 1) * nrw > kFwdMaxGroupWarps || nrw * eg > 16)) --eg;
+  return eg;
+}
+
 template <int NT, int MODE>
 static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cudaStream_t s) {
   const int xs_stride = g.fz_stride;
@@ -981,19 +1020,24 @@ static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cu
   const int ecap = 3 * nrows + 8;  // a line crosses at most two pixels per row of its dominant axis
   const int rpp = forward_runs_per_part(g);
   const int parts = (g.n_runs + rpp - 1) / rpp;
-  const int threads = 32 * ((std::min(rpp, g.n_runs) + kRunsPerWarp - 1) / kRunsPerWarp);
+  const int nrw = (std::min(rpp, g.n_runs) + kRunsPerWarp - 1) / kRunsPerWarp;  // warps per entry group
+  const int egroups = forward_entry_groups(g);
+  if (egroups < 1 || (egroups - 1) * nrw > kFwdMaxGroupWarps || nrw * egroups > 16) return cudaErrorInvalidValue;
+  const int threads = 32 * nrw * egroups;
   // a block computes the taps of the components of the segments its runs span
   const int ncomp_tab = g.max_part_comps[rpp / kRunsPerWarp];
   // entries per chunk: 32, fewer when a block holds the taps of many components (mashing)
   int chunk = kFwdChunk;
   while (chunk > 4 && (size_t)2 * ncomp_tab * chunk * sizeof(TapRecT<NT>) > 48 * 1024) chunk /= 2;
   const size_t smem = (size_t)2 * chunk * xs_stride * sizeof(float) +
-                      (size_t)2 * ncomp_tab * chunk * sizeof(TapRecT<NT>) + (size_t)ecap * sizeof(Entry);
+                      (size_t)2 * ncomp_tab * chunk * sizeof(TapRecT<NT>) + (size_t)ecap * sizeof(Entry) +
+                      (size_t)(egroups - 1) * nrw * kRunsPerWarp * 32 * sizeof(float);
   if (smem > 200 * 1024 || (size_t)chunk * xs_stride >= ((size_t)1 << kOffBits)) return cudaErrorInvalidValue;
   if (MODE == FWD_DATA && !a.sigma) return cudaErrorInvalidValue;
   if ((MODE == FWD_DATA || MODE == FWD_EM) && (!a.b || !a.r || !a.wdy)) return cudaErrorInvalidValue;
+  auto kern = egroups > 1 ? k_forward<NT, MODE, true> : k_forward<NT, MODE, false>;
   {
-    cudaError_t e = allow_dynamic_smem(k_forward<NT, MODE>, smem);
+    cudaError_t e = allow_dynamic_smem(kern, smem);
     if (e != cudaSuccess) return e;
   }
   const int lines = subset_views(g, subset) * g.R;
@@ -1003,7 +1047,7 @@ static cudaError_t fwd_launch(const DevGeom& g, int subset, const FwdArgs& a, cu
                      (size_t)lines * parts > a.ticket_cap))
     return cudaErrorInvalidValue;
   dim3 grid(lines, rsplit, parts);
-  k_forward<NT, MODE><<<grid, threads, smem, s>>>(g, subset, ecap, rsplit, xs_stride, rpp, ncomp_tab, chunk, a);
+  kern<<<grid, threads, smem, s>>>(g, subset, ecap, rsplit, xs_stride, rpp, ncomp_tab, chunk, egroups, a);
   return cudaGetLastError();
 }
 

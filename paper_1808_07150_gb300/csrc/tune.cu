@@ -124,6 +124,13 @@ extern "C" int spdhg_autotune(spdhg_ctx* ctx, int reps, int* chosen, void* strea
     knobs.push_back(k);
   }
   {
+    // entry groups only where a line's plane runs leave the block with few warps
+    Knob k{SPDHG_TUNE_FWD_GROUPS, true, {}};
+    if (g.n_runs <= 6)
+      for (int eg : {1, 2, 4, 8}) k.values.push_back(eg);
+    knobs.push_back(k);
+  }
+  {
     Knob k{SPDHG_TUNE_FWD_SPLIT, true, {}};
     for (int sp : {1, 2, 4, 8})
       if (sp == 1 || nrows / sp >= 32) k.values.push_back(sp);

@@ -167,6 +167,7 @@ def test_autotune_keeps_state_and_parity(kind):
             np.testing.assert_array_equal(after[k], before[k], err_msg=k)
         assert chosen["fwd_warps"] in (0, 2, 4, 8, 16)
         assert chosen["fwd_split"] in (0, 1, 2, 4, 8)
+        assert chosen["fwd_groups"] in (0, 1, 2, 4, 8)
         if kind == "dtv":
             assert 2 <= chosen["prior_cols"] <= 32 and chosen["prior_ychunk"] in (16, 32, 64, 128, 256)
             assert chosen["prior_stages"] in (3, 4)
@@ -204,3 +205,4 @@ def test_backprojector_item_table_is_bit_identical(sc):
             out.append({k: host(v) for k, v in st.items()})
     for k in out[0]:
         np.testing.assert_array_equal(out[0][k], out[1][k], err_msg=k)
+

@@ -58,6 +58,28 @@ def test_project_and_backproject_match_oracle(sc):
             assert abs(lhs - rhs) <= 2e-6 * abs(lhs)
 
 
+@pytest.mark.parametrize("groups,split", [(1, 1), (2, 1), (4, 1), (8, 1), (3, 2), (4, 4)])
+@pytest.mark.parametrize("sc", [synth.tiny_3d(steep=True), synth.config_2d(), synth.config_3d()],
+                         ids=lambda s: s.name)
+def test_forward_entry_groups_match_oracle(sc, groups, split):
+    """The forward projector with several warps sharing each plane run (entry groups, alone and
+    with row parts) against the oracle, on every plane of the first subset."""
+    import torch
+    mult = synth.smooth_multipliers(sc, 9)
+    x = synth.random_image(sc, 1)
+    with _ctx(sc, mult) as ctx:
+        ctx.spdhg_tune("fwd_groups", groups)
+        ctx.spdhg_tune("fwd_split", split)
+        y_gpu = torch.zeros(sc.n_bins, device="cuda")
+        ctx.spdhg_project(dev(x), y_gpu, 0)
+        torch.cuda.synchronize()
+    mask = O.subset_mask(sc, 0)
+    y_ref = O.project(sc, x.astype(np.float64), 0, mult.astype(np.float64))
+    assert rel(host(y_gpu)[mask.ravel()], y_ref[mask]) < 1e-5
+    assert maxerr(host(y_gpu)[mask.ravel()], y_ref[mask]) < 1e-5
+    assert np.all(host(y_gpu)[~mask.ravel()] == 0.0)
+
+
 @pytest.mark.parametrize("sc", [synth.tiny_3d(steep=True), wide_2d(), synth.config_2d()], ids=lambda s: s.name)
 def test_sigma_and_T_match_oracle(sc):
     import paper_1808_07150_gb300 as pkg
