@@ -1001,15 +1001,22 @@ def run_configs(args):
 
 
 def run_ncu_case():
-    """Few launches on the full workload: setup (252 sensitivity backprojections), then one data
-    iteration (k_forward, k_backward) and one dTV prior iteration (k_prior)."""
+    """Few launches with the per-launch work of the full workload on a few GB of device memory:
+    the mMR-scale image and geometry with 28 views in 28 subsets (one view per subset, as in the
+    252-subset workload; the backprojector's item table 28/252 of its full size).  Setup (28
+    sensitivity backprojections, one sigma projection), then one data iteration (k_forward,
+    k_backward; subset 1, the view at 6.4 degrees) and one dTV prior iteration (k_prior)."""
+    import dataclasses
+
     import torch
 
     import paper_1808_07150_gb300 as pkg
+    import synth
     from paper_1808_07150_gb300 import _build_ext
     torch.cuda.set_device(0)
     _build_ext.build()
-    sc, d = make_workload()
+    sc = dataclasses.replace(synth.config_mmr(), n_views=28, n_subsets=28, name="mmr-28v")
+    d = synth.make_problem(sc, SEED, counts=4e8 * 28 / 252, bg_frac=0.1, with_mult=True, with_side=True)
     dev = torch.device("cuda", 0)
 
     def to_dev(a):
@@ -1018,7 +1025,7 @@ def run_ncu_case():
     with pkg.Context(sc) as ctx:
         ctx.spdhg_set_data(to_dev(d["b"]), to_dev(d["r"]), to_dev(d["mult"]), to_dev(d["side"]))
         ctx.spdhg_setup(pkg.make_params("dtv", alpha=ALPHA, dtv_gamma=0.995, dtv_eta_frac=0.01, seed=SEED))
-        ctx.spdhg_iterate([5, sc.n_subsets])
+        ctx.spdhg_iterate([1, sc.n_subsets])
         torch.cuda.synchronize()
     print("ncu case done")
     return 0

@@ -296,6 +296,8 @@ enum { SPDHG_TUNE_PRIOR_COLS = 0,   /* prior kernel: voxel columns per block, in
                                        taking every k-th pixel entry of the line (1 .. 8; their
                                        partial sums are added in a fixed order); 0 = enough for
                                        four warps per block when a line has few plane runs */
+       SPDHG_TUNE_PRIOR_VZ = 7,     /* prior kernel: voxels per thread along z (1, 2 or 4;
+                                       0 = 1) */
        SPDHG_TUNE_KNOBS = 8 };
 
 /* Sets one launch-shape knob of the context (value 0: default).  Out-of-range values are rejected

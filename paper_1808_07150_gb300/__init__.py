@@ -187,7 +187,7 @@ class Context:
 
     def spdhg_tune(self, knob, value):
         """Sets a launch-shape knob ('prior_cols', 'prior_ychunk', 'fwd_split', 'fwd_warps', 'prior_stages',
-        'bwd_table', 'fwd_groups'); 0 = default."""
+        'bwd_table', 'fwd_groups', 'prior_vz'); 0 = default."""
         code = _capi.TUNE[knob] if isinstance(knob, str) else int(knob)
         self._check(_capi.lib().spdhg_tune(self.h, code, int(value)))
 

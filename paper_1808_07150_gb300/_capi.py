@@ -31,7 +31,7 @@ _EXPORTS = [
     "unet_set_params", "unet_init", "unet_get_params", "unet_get_grads", "unet_forward", "unet_backward", "unet_adam_step",
 ]
 TUNE = {"prior_cols": 0, "prior_ychunk": 1, "fwd_split": 2, "fwd_warps": 3, "prior_stages": 4, "bwd_table": 5,
-        "fwd_groups": 6}
+        "fwd_groups": 6, "prior_vz": 7}
 TUNE_KNOBS = 8
 KERNELS = ["forward", "backward", "prior", "tgv", "w_step"]
 

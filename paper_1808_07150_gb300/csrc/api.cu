@@ -1387,10 +1387,14 @@ int spdhg_osem(spdhg_ctx* ctx, const spdhg_params* params, int mlem, float* x_in
 
 int spdhg_tune(spdhg_ctx* ctx, int knob, int value) {
   if (!ctx || knob < 0 || knob >= SPDHG_TUNE_KNOBS || value < 0) return SPDHG_ERR_ARG;
-  const int zw = (ctx->dg.nz + 31) / 32;
   switch (knob) {
     case SPDHG_TUNE_PRIOR_COLS:
-      if (value != 0 && (value < 2 || value * zw > 32)) return fail(ctx, SPDHG_ERR_ARG, "prior cols out of range");
+      // the launch checks cols against the warps of a column at the current voxels per thread
+      if (value != 0 && (value < 2 || value > 32)) return fail(ctx, SPDHG_ERR_ARG, "prior cols out of range");
+      break;
+    case SPDHG_TUNE_PRIOR_VZ:
+      if (value != 0 && value != 1 && value != 2 && value != 4)
+        return fail(ctx, SPDHG_ERR_ARG, "prior voxels per thread must be 1, 2 or 4");
       break;
     case SPDHG_TUNE_PRIOR_STAGES:
       if (value != 0 && value != 3 && value != 4) return fail(ctx, SPDHG_ERR_ARG, "prior stages must be 3 or 4");

@@ -175,6 +175,8 @@ struct PriorArgs {
   float sigma, alpha, inv_p, gamma_d, eta2;
 };
 cudaError_t launch_prior(const DevGeom& g, const PriorArgs& a, cudaStream_t s);
+// whether the prior kernel's launch-shape knobs fit together (voxels per thread, columns, rows)
+bool prior_launch_ok(const DevGeom& g, int kind);
 
 struct TgvArgs {
   int block;             // 0: A = (grad, -I), 1: A = (0, E)

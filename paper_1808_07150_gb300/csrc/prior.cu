@@ -61,59 +61,82 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Row pipeline depth STAGES: rows iy and iy + 1 are used, the next STAGES - 2 rows are loading.
+// Row pipeline depth STAGES: rows iy and iy + 1 of x (and v) are used, the next STAGES - 2 rows
+// are loading.
 
 // One block owns `cols - 1` voxel columns in x (plus one halo column on the lower side whose
-// duals are recomputed, not written) and the whole z extent (warps along z, so every access is
-// a contiguous 128-byte line), and marches along y over `ychunk` rows (plus one warm-up row).
-// Rows are staged in shared memory by a STAGES-deep cp.async pipeline: each thread copies its own
-// voxel's operands (x, v also for one upper halo column), neighbours are read from the staged
-// rows, the lower y neighbour's dual change is carried in a register and the lower x / z
-// neighbours' through shared memory.  Every array is read from HBM once per row.
-template <int KIND, int STAGES>
+// duals are recomputed, not written) and the whole z extent, and marches along y over `ychunk`
+// rows (plus one warm-up row).  A thread holds VZ voxels of one column, z = z0 + lane + 32 k
+// (k < VZ), so every warp access is a contiguous 128-byte line and the per-row work of the
+// thread (addresses, barriers, pipeline control) is shared by VZ voxels.  x and v, whose
+// neighbours other threads need, are staged in shared memory by a STAGES-deep cp.async pipeline
+// (each thread copies its own voxels, the halo warps also one upper halo column); q, z and T are
+// read by their own thread only and go straight into registers, one row ahead.  The lower y
+// neighbour's dual change is carried in a register and the lower x / z neighbours' through
+// shared memory.  Every array is read from HBM once per row.
+template <int KIND, int STAGES, int VZ>
 __global__ void __launch_bounds__(1024) k_prior(DevGeom g, PriorArgs a, int cols, int ychunk) {
   extern __shared__ float sh[];
-  const int zw = (g.nz + 31) >> 5;
-  const int zc = zw * 32;                     // staged z extent
+  const int zw = (g.nz + 32 * VZ - 1) / (32 * VZ);  // warps per column
+  const int zc = zw * 32 * VZ;                      // staged z extent
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int c = w / zw, zi = w - c * zw;
-  const int iz = zi * 32 + lane;
+  const int iz0 = zi * 32 * VZ + lane;              // voxel k of this thread: iz0 + 32 k
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int N = nx * ny * nz;
   const int sy = nx * nz;
-  const int x0 = blockIdx.x * (cols - 1) - 1;  // x of column 0 (the lower halo)
+  const int x0 = blockIdx.x * (cols - 1) - 1;       // x of column 0 (the lower halo)
   const int ix = x0 + c;
-  const bool live = ix >= 0 && ix < nx && iz < nz;
-  const bool owner = live && c >= 1;
+  const bool col_live = ix >= 0 && ix < nx;
+  const bool col_owner = col_live && c >= 1;
   const int y0 = blockIdx.y * ychunk, y1 = min(ny, y0 + ychunk);
-  const int ys = y0 > 0 ? y0 - 1 : 0;         // first row computed (warm-up row for y0 > 0)
-  const int ylast = min(y1, ny - 1);          // last row whose x / v are needed
-  const bool hx = ix < nx - 1, hz = iz < nz - 1;
+  const int ys = y0 > 0 ? y0 - 1 : 0;               // first row computed (warm-up row for y0 > 0)
+  const int ylast = min(y1, ny - 1);                // last row whose x / v are needed
+  const bool hx = ix < nx - 1;
   const bool dtv = KIND == SPDHG_PRIOR_DTV;
+  const int ixh = x0 + cols;                        // upper halo column (x, v only)
+  const bool colh = ixh < nx;
 
-  // stage layout: x, v: (cols + 1) x zc; q0, q1, q2, z, T: cols x zc
-  const int xv_sz = (cols + 1) * zc, cell_sz = cols * zc;
-  const int stage_sz = 2 * xv_sz + 5 * cell_sz;
-  float* sbx = sh + STAGES * stage_sz;        // [cols][zc] b_x of the current row
-  float* sbz = sbx + cell_sz;                 // [cols][zc] b_z of the current row
-  const int me = c * zc + iz;
+  // stage layout per row: x, v: (cols + 1) x zc
+  const int xv_sz = (cols + 1) * zc;
+  const int stage_sz = dtv ? 2 * xv_sz : xv_sz;
+  float* sbx = sh + STAGES * stage_sz;              // [cols][zc] b_x of the current row
+  float* sbz = sbx + cols * zc;                     // [cols][zc] b_z of the current row
+  const int me = c * zc + iz0;
 
   auto issue_row = [&](int row) {
     float* st = sh + (row % STAGES) * stage_sz;
-    const int base = row * sy + ix * nz + iz;  // only dereferenced when valid
-    cp_async4(st + me, a.x_in, base, live);
-    if (dtv) cp_async4(st + xv_sz + me, a.side, base, live);
-    cp_async4(st + 2 * xv_sz + me, a.q_in, base, live);
-    cp_async4(st + 2 * xv_sz + cell_sz + me, a.q_in, N + base, live);
-    cp_async4(st + 2 * xv_sz + 2 * cell_sz + me, a.q_in, 2 * N + base, live);
-    cp_async4(st + 2 * xv_sz + 3 * cell_sz + me, a.z, base, owner);
-    cp_async4(st + 2 * xv_sz + 4 * cell_sz + me, a.T, base, owner);
+    const int base = row * sy + ix * nz + iz0;      // only dereferenced when valid
+#pragma unroll
+    for (int k = 0; k < VZ; ++k) {
+      const bool lv = col_live && iz0 + 32 * k < nz;
+      cp_async4(st + me + 32 * k, a.x_in, base + 32 * k, lv);
+      if (dtv) cp_async4(st + xv_sz + me + 32 * k, a.side, base + 32 * k, lv);
+    }
     if (c == 0) {  // upper halo column: x and v of x0 + cols
-      const int ixh = x0 + cols;
-      const bool vh = ixh < nx && iz < nz;
-      const int bh = row * sy + ixh * nz + iz;
-      cp_async4(st + cols * zc + iz, a.x_in, bh, vh);
-      if (dtv) cp_async4(st + xv_sz + cols * zc + iz, a.side, bh, vh);
+      const int bh = row * sy + ixh * nz + iz0;
+#pragma unroll
+      for (int k = 0; k < VZ; ++k) {
+        const bool vh = colh && iz0 + 32 * k < nz;
+        cp_async4(st + cols * zc + iz0 + 32 * k, a.x_in, bh + 32 * k, vh);
+        if (dtv) cp_async4(st + xv_sz + cols * zc + iz0 + 32 * k, a.side, bh + 32 * k, vh);
+      }
+    }
+  };
+  // q of every live voxel (the halo column's duals are recomputed), z and T of the owned ones
+  float qr[VZ][3], zr[VZ], Tr[VZ];
+  auto load_regs = [&](int row) {
+    const int base = row * sy + ix * nz + iz0;
+#pragma unroll
+    for (int k = 0; k < VZ; ++k) {
+      const bool lv = col_live && iz0 + 32 * k < nz;
+      const bool ow = lv && c >= 1;
+      const int i = base + 32 * k;
+      qr[k][0] = lv ? a.q_in[i] : 0.f;
+      qr[k][1] = lv ? a.q_in[N + i] : 0.f;
+      qr[k][2] = lv ? a.q_in[2 * N + i] : 0.f;
+      zr[k] = ow ? a.z[i] : 0.f;
+      Tr[k] = ow ? a.T[i] : 0.f;
     }
   };
 
@@ -121,73 +144,117 @@ __global__ void __launch_bounds__(1024) k_prior(DevGeom g, PriorArgs a, int cols
     if (ys + k <= ylast) issue_row(ys + k);
     cp_async_commit();
   }
-  float by_prev = 0.f;
+  load_regs(ys);
+  float by_prev[VZ];
+#pragma unroll
+  for (int k = 0; k < VZ; ++k) by_prev[k] = 0.f;
   for (int iy = ys; iy < y1; ++iy) {
     if (iy + STAGES - 1 <= ylast) issue_row(iy + STAGES - 1);
     cp_async_commit();
-    cp_async_wait<STAGES - 2>();  // rows iy and iy + 1 have landed
+    // this row's q, z, T; the next row's are requested before this row's arithmetic
+    float qo[VZ][3], zo[VZ], To[VZ];
+#pragma unroll
+    for (int k = 0; k < VZ; ++k) {
+      qo[k][0] = qr[k][0];
+      qo[k][1] = qr[k][1];
+      qo[k][2] = qr[k][2];
+      zo[k] = zr[k];
+      To[k] = Tr[k];
+    }
+    if (iy + 1 < y1) load_regs(iy + 1);
+    cp_async_wait<STAGES - 2>();  // rows iy and iy + 1 of x, v have landed
     __syncthreads();
     const float* st = sh + (iy % STAGES) * stage_sz;
     const float* sn = sh + ((iy + 1) % STAGES) * stage_sz;
     const bool hy = iy < ny - 1;
-    float b[3] = {0.f, 0.f, 0.f}, qn[3] = {0.f, 0.f, 0.f};
-    const float xc = st[me];
-    if (live) {
-      const float gr[3] = {hx ? st[me + zc] - xc : 0.f, hy ? sn[me] - xc : 0.f, hz ? st[me + 1] - xc : 0.f};
-      float gv[3] = {0.f, 0.f, 0.f};
-      if (dtv) {
-        const float* sv = st + xv_sz;
-        const float vc = sv[me];
-        gv[0] = hx ? sv[me + zc] - vc : 0.f;
-        gv[1] = hy ? sn[xv_sz + me] - vc : 0.f;
-        gv[2] = hz ? sv[me + 1] - vc : 0.f;
+    float b[VZ][3], qn[VZ][3], xc[VZ];
+#pragma unroll
+    for (int k = 0; k < VZ; ++k) {
+      const int iz = iz0 + 32 * k, m = me + 32 * k;
+      const bool lv = col_live && iz < nz, hz = iz < nz - 1;
+      b[k][0] = b[k][1] = b[k][2] = 0.f;
+      qn[k][0] = qn[k][1] = qn[k][2] = 0.f;
+      xc[k] = st[m];
+      if (lv) {
+        const float gr[3] = {hx ? st[m + zc] - xc[k] : 0.f, hy ? sn[m] - xc[k] : 0.f, hz ? st[m + 1] - xc[k] : 0.f};
+        float gv[3] = {0.f, 0.f, 0.f};
+        if (dtv) {
+          const float* sv = st + xv_sz;
+          const float vc = sv[m];
+          gv[0] = hx ? sv[m + zc] - vc : 0.f;
+          gv[1] = hy ? sn[xv_sz + m] - vc : 0.f;
+          gv[2] = hz ? sv[m + 1] - vc : 0.f;
+        }
+        dual_update<KIND>(a, gr, gv, qo[k], b[k], qn[k]);
       }
-      const float* sq = st + 2 * xv_sz;
-      const float qo[3] = {sq[me], sq[cell_sz + me], sq[2 * cell_sz + me]};
-      dual_update<KIND>(a, gr, gv, qo, b, qn);
+      sbx[m] = b[k][0];
+      sbz[m] = b[k][2];
     }
-    sbx[me] = b[0];
-    sbz[me] = b[2];
     __syncthreads();
-    if (owner && iy >= y0) {
-      const int idx = iy * sy + ix * nz + iz;
-      a.q_out[idx] = qn[0];
-      a.q_out[N + idx] = qn[1];
-      a.q_out[2 * N + idx] = qn[2];
-      // dz = A_n^T dq = sum_a [k_a >= 1] b_a(k - e_a) - [k_a < n_a - 1] b_a(k)
-      float dz = 0.f;
-      if (ix > 0) dz += sbx[me - zc];
-      if (iy > 0) dz += by_prev;
-      if (iz > 0) dz += sbz[me - 1];
-      if (hx) dz -= b[0];
-      if (hy) dz -= b[1];
-      if (hz) dz -= b[2];
-      const float* sq = st + 2 * xv_sz;
-      const float zn = sq[3 * cell_sz + me] + dz;
-      a.z[idx] = zn;
-      a.x_out[idx] = prox_nonneg(xc - sq[4 * cell_sz + me] * fmaf(dz, a.inv_p, zn));
+    if (col_owner && iy >= y0) {
+#pragma unroll
+      for (int k = 0; k < VZ; ++k) {
+        const int iz = iz0 + 32 * k, m = me + 32 * k;
+        if (iz >= nz) continue;
+        const int idx = iy * sy + ix * nz + iz;
+        a.q_out[idx] = qn[k][0];
+        a.q_out[N + idx] = qn[k][1];
+        a.q_out[2 * N + idx] = qn[k][2];
+        // dz = A_n^T dq = sum_a [k_a >= 1] b_a(k - e_a) - [k_a < n_a - 1] b_a(k)
+        float dz = 0.f;
+        if (ix > 0) dz += sbx[m - zc];
+        if (iy > 0) dz += by_prev[k];
+        if (iz > 0) dz += sbz[m - 1];
+        if (hx) dz -= b[k][0];
+        if (hy) dz -= b[k][1];
+        if (iz < nz - 1) dz -= b[k][2];
+        const float zn = zo[k] + dz;
+        a.z[idx] = zn;
+        a.x_out[idx] = prox_nonneg(xc[k] - To[k] * fmaf(dz, a.inv_p, zn));
+      }
     }
-    by_prev = b[1];
+#pragma unroll
+    for (int k = 0; k < VZ; ++k) by_prev[k] = b[k][1];
     __syncthreads();  // stage iy % S is refilled by the next iteration's copy
   }
   cp_async_wait<0>();
 }
 
-cudaError_t launch_prior(const DevGeom& g, const PriorArgs& a, cudaStream_t s) {
-  const int zw = (g.nz + 31) / 32;
-  if (zw > 16) return cudaErrorInvalidValue;
-  // default: up to 8 columns per block (7 owned + 1 halo; at most 32 warps), and enough row
-  // chunks for about one block per SM (the blocks are large: one wave, no tail)
+// voxels per thread along z (more columns per block: a smaller halo share, but fewer blocks)
+static int prior_vz(const DevGeom& g) { return g.tune[SPDHG_TUNE_PRIOR_VZ] ? g.tune[SPDHG_TUNE_PRIOR_VZ] : 1; }
+
+// launch shape of the prior kernel at the current knobs; false where they do not fit together
+static bool prior_shape(const DevGeom& g, bool dtv, int* vz_out, int* zw_out, int* cols_out, int* ychunk_out,
+                        int* stages_out, size_t* smem_out) {
+  const int vz = prior_vz(g);
+  if (vz != 1 && vz != 2 && vz != 4) return false;
+  const int zw = (g.nz + 32 * vz - 1) / (32 * vz);
+  if (zw > 16) return false;
   const int cols = g.tune[SPDHG_TUNE_PRIOR_COLS] ? g.tune[SPDHG_TUNE_PRIOR_COLS]
-                                                 : std::max(2, std::min(std::min(8, 32 / zw), g.nx + 1));
+                                                 : std::max(2, std::min(std::min(16, 32 / zw), g.nx + 1));
   const int gx = (g.nx + cols - 2) / (cols - 1);
   const int chunks = std::max(1, std::min(g.ny, 152 / gx));
   const int ychunk = g.tune[SPDHG_TUNE_PRIOR_YCHUNK] ? g.tune[SPDHG_TUNE_PRIOR_YCHUNK] : (g.ny + chunks - 1) / chunks;
   const int stages = g.tune[SPDHG_TUNE_PRIOR_STAGES] ? g.tune[SPDHG_TUNE_PRIOR_STAGES] : 4;
-  if (cols * zw > 32 || (stages != 3 && stages != 4)) return cudaErrorInvalidValue;
-  const int zc = zw * 32;
-  const size_t stage = (size_t)2 * (cols + 1) * zc + (size_t)5 * cols * zc;
+  if (cols * zw > 32 || (stages != 3 && stages != 4)) return false;
+  const size_t zc = (size_t)zw * 32 * vz;
+  const size_t stage = (size_t)(dtv ? 2 : 1) * (cols + 1) * zc;
   const size_t smem = (stages * stage + 2 * (size_t)cols * zc) * sizeof(float);
+  if (smem > 227 * 1024) return false;
+  *vz_out = vz; *zw_out = zw; *cols_out = cols; *ychunk_out = ychunk; *stages_out = stages; *smem_out = smem;
+  return true;
+}
+
+bool prior_launch_ok(const DevGeom& g, int kind) {
+  int vz, zw, cols, ychunk, stages;
+  size_t smem;
+  return prior_shape(g, kind == SPDHG_PRIOR_DTV, &vz, &zw, &cols, &ychunk, &stages, &smem);
+}
+
+cudaError_t launch_prior(const DevGeom& g, const PriorArgs& a, cudaStream_t s) {
+  int vz, zw, cols, ychunk, stages;
+  size_t smem;
+  if (!prior_shape(g, a.kind == SPDHG_PRIOR_DTV, &vz, &zw, &cols, &ychunk, &stages, &smem)) return cudaErrorInvalidValue;
   dim3 grid((g.nx + cols - 2) / (cols - 1), (g.ny + ychunk - 1) / ychunk);
   const int threads = cols * zw * 32;
   auto launch = [&](auto kern) -> cudaError_t {
@@ -196,13 +263,19 @@ cudaError_t launch_prior(const DevGeom& g, const PriorArgs& a, cudaStream_t s) {
     kern<<<grid, threads, smem, s>>>(g, a, cols, ychunk);
     return cudaGetLastError();
   };
-  const bool s3 = stages == 3;
+  auto by_shape = [&](auto k31, auto k32, auto k34, auto k41, auto k42, auto k44) -> cudaError_t {
+    if (stages == 3) return vz == 1 ? launch(k31) : (vz == 2 ? launch(k32) : launch(k34));
+    return vz == 1 ? launch(k41) : (vz == 2 ? launch(k42) : launch(k44));
+  };
+#define SPDHG_PRIOR_SHAPES(K) \
+  k_prior<K, 3, 1>, k_prior<K, 3, 2>, k_prior<K, 3, 4>, k_prior<K, 4, 1>, k_prior<K, 4, 2>, k_prior<K, 4, 4>
   switch (a.kind) {
-    case SPDHG_PRIOR_TV: return s3 ? launch(k_prior<SPDHG_PRIOR_TV, 3>) : launch(k_prior<SPDHG_PRIOR_TV, 4>);
-    case SPDHG_PRIOR_DTV: return s3 ? launch(k_prior<SPDHG_PRIOR_DTV, 3>) : launch(k_prior<SPDHG_PRIOR_DTV, 4>);
-    case SPDHG_PRIOR_ATV: return s3 ? launch(k_prior<SPDHG_PRIOR_ATV, 3>) : launch(k_prior<SPDHG_PRIOR_ATV, 4>);
+    case SPDHG_PRIOR_TV: return by_shape(SPDHG_PRIOR_SHAPES(SPDHG_PRIOR_TV));
+    case SPDHG_PRIOR_DTV: return by_shape(SPDHG_PRIOR_SHAPES(SPDHG_PRIOR_DTV));
+    case SPDHG_PRIOR_ATV: return by_shape(SPDHG_PRIOR_SHAPES(SPDHG_PRIOR_ATV));
     default: return cudaErrorInvalidValue;
   }
+#undef SPDHG_PRIOR_SHAPES
 }
 
 // ---------------------------------------------------------------------------------------

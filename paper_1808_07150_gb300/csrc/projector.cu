@@ -561,9 +561,40 @@ struct PixItem {
   PixInt I;
 };
 
-constexpr int kBwdTile = 4;              // block = kBwdTile x kBwdTile voxel columns, one warp each
-constexpr int kBwdWarps = kBwdTile * kBwdTile;
+constexpr int kBwdTileX = 4;             // block = kBwdTileX x kBwdTileY voxel columns, one warp each
+constexpr int kBwdTileY = 4;
+constexpr int kBwdWarps = kBwdTileX * kBwdTileY;
+constexpr int kBwdBlocksPerSM = 64 / kBwdWarps;      // resident blocks, up to 128 slices (4 voxels a lane)
+constexpr int kBwdBlocksPerSM8 = 48 / kBwdWarps;     // more slices (8 accumulators a lane)
 constexpr int kBwdMaxItems = 64;         // (pair, segment) items per column and view
+
+// Gather of one column's items on an unmashed geometry, bucket b holding the items with b + 1
+// taps: voxel iz (lane + 32 k) adds sum_t L_t sw[x + iz + t] where its first tap's plane
+// iz + j0 lies in [-PAD, n) (the segment's frames supply the zeros of the other taps).
+template <int NT, int ZK>
+__device__ __forceinline__ void gather_items(const float* sw, const float4* myL, const int4* myM, const int* bs,
+                                             int lane, float* acc) {
+#pragma unroll
+  for (int b = 0; b < NT; ++b) {
+    for (int it = bs[b]; it < bs[b + 1]; ++it) {
+      const float4 Lv = myL[it];
+      const int4 M = myM[it];
+      const float* src0 = sw + M.x;
+#pragma unroll
+      for (int k = 0; k < ZK; ++k) {
+        const int iz = lane + 32 * k;
+        if ((unsigned)(iz + M.y) < (unsigned)M.z) {
+          const float* src = src0 + iz;
+          float sum = Lv.x * src[0];
+          if (b >= 1) sum = fmaf(Lv.y, src[1], sum);
+          if (b >= 2) sum = fmaf(Lv.z, src[2], sum);
+          if (b >= 3) sum = fmaf(Lv.w, src[3], sum);
+          acc[k] += sum;
+        }
+      }
+    }
+  }
+}
 
 // Backprojection.  A block owns a 4 x 4 tile of voxel columns; for each view of the subset it
 // stages the contiguous radial rows w[view][r_min..r_max][0..P) that the tile's footprints
@@ -574,7 +605,7 @@ constexpr int kBwdMaxItems = 64;         // (pair, segment) items per column and
 // runs from shared memory, lane = iz mod 32, ZK voxels per lane.  Up to 128 slices (ZK <= 4) four
 // blocks share an SM (32 registers per thread); with eight accumulators per lane, three.
 template <int NT, int ZK, int MODE, bool MASHED, bool TAB>
-__global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(DevGeom g, int subset, int nr_tile, int p_pad,
+__global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? kBwdBlocksPerSM : kBwdBlocksPerSM8) k_backward(DevGeom g, int subset, int nr_tile, int p_pad,
                                                              int bcap, int cpb, BwdArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int PAD = NT - 1;
@@ -590,16 +621,29 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
   PixItem* mypix = pix + wi * g.nr_max;
   const int nviews = subset_views(g, subset);
   const int nz = g.nz;
-  const int tx0 = blockIdx.x * kBwdTile, ty0 = blockIdx.y * kBwdTile;
-  const int ix = tx0 + (wi % kBwdTile), iy = ty0 + (wi / kBwdTile);
+  const int tx0 = blockIdx.x * kBwdTileX, ty0 = blockIdx.y * kBwdTileY;
+  const int ix = tx0 + (wi % kBwdTileX), iy = ty0 + (wi / kBwdTileX);
   const bool live = ix < g.nx && iy < g.ny;
   const float Xc = (float)ix + 0.5f - 0.5f * (float)g.nx;
   const float Yc = (float)iy + 0.5f - 0.5f * (float)g.ny;
   const float X0 = (float)tx0 + 0.5f - 0.5f * (float)g.nx, Y0 = (float)ty0 + 0.5f - 0.5f * (float)g.ny;
-  const float X1 = X0 + (float)(kBwdTile - 1), Y1 = Y0 + (float)(kBwdTile - 1);
+  const float X1 = X0 + (float)(kBwdTileX - 1), Y1 = Y0 + (float)(kBwdTileY - 1);
   float acc[ZK];
 #pragma unroll
   for (int k = 0; k < ZK; ++k) acc[k] = 0.f;
+  if constexpr (MODE == BWD_UPDATE) {
+    // the epilogue's x, z, T lines of the block's columns are requested into L2 now, so that
+    // their DRAM reads overlap the staging and the gather
+    const int lines = (nz + 31) / 32;
+    for (int q = threadIdx.x; q < kBwdWarps * 3 * lines; q += blockDim.x) {
+      const int col = q / (3 * lines), rem = q - col * 3 * lines, arr = rem / lines, seg = rem - arr * lines;
+      const int cx = tx0 + (col % kBwdTileX), cy = ty0 + (col / kBwdTileX);
+      if (cx < g.nx && cy < g.ny) {
+        const float* base = arr == 0 ? (const float*)a.x : (arr == 1 ? (const float*)a.z : a.T);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(base + ((size_t)cy * g.nx + cx) * nz + 32 * seg));
+      }
+    }
+  }
   // padded position of every plane, and the zero frames of the staged rows (written once)
   for (int p = threadIdx.x; p < g.P; p += blockDim.x) seg_of[p] = p + (2 * g.plane_seg[p] + 1) * PAD;
   if constexpr (PAD > 0) {
@@ -732,26 +776,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
     }
     // 4. gather: one branch-free loop per tap count
     if (live && !MASHED) {
-#pragma unroll
-      for (int b = 0; b < NT; ++b) {
-        for (int it = bs[b]; it < bs[b + 1]; ++it) {
-          const float4 Lv = myL[it];
-          const int4 M = myM[it];
-          const float* src0 = sw + M.x;
-#pragma unroll
-          for (int k = 0; k < ZK; ++k) {
-            const int iz = lane + 32 * k;
-            if ((unsigned)(iz + M.y) < (unsigned)M.z) {
-              const float* src = src0 + iz;
-              float sum = Lv.x * src[0];
-              if (b >= 1) sum = fmaf(Lv.y, src[1], sum);
-              if (b >= 2) sum = fmaf(Lv.z, src[2], sum);
-              if (b >= 3) sum = fmaf(Lv.w, src[3], sum);
-              acc[k] += sum;
-            }
-          }
-        }
-      }
+      gather_items<NT, ZK>(sw, myL, myM, bs, lane, acc);
     } else if (live) {
       // mashed: tap t of voxel iz counts when its plane includes the component
 #pragma unroll
@@ -777,7 +802,10 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? 4 : 3) k_backward(De
     }
     if (MASHED) __syncwarp();  // the items are replaced by the next batch's
     }  // component batches
-    __syncthreads();  // the staged rows are replaced by the next view's
+    // the staged rows are replaced by the next view's; after the last view each warp goes on to
+    // its epilogue as soon as its own gather is done, so that the early warps' loads and stores
+    // overlap the others' gathers
+    if (l + 1 < nviews) __syncthreads();
   }
   if (!live) return;
 #pragma unroll
@@ -817,13 +845,13 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_bwd_items(DevGeom g, int nr_
   __shared__ PixItem pix[kBwdWarps][kTabMaxPairs];
   constexpr int PAD = NT - 1;
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  const int tx0 = blockIdx.x * kBwdTile, ty0 = blockIdx.y * kBwdTile;
-  const int ix = tx0 + (wi % kBwdTile), iy = ty0 + (wi / kBwdTile);
+  const int tx0 = blockIdx.x * kBwdTileX, ty0 = blockIdx.y * kBwdTileY;
+  const int ix = tx0 + (wi % kBwdTileX), iy = ty0 + (wi / kBwdTileX);
   const bool live = ix < g.nx && iy < g.ny;
   const float Xc = (float)ix + 0.5f - 0.5f * (float)g.nx;
   const float Yc = (float)iy + 0.5f - 0.5f * (float)g.ny;
   const float X0 = (float)tx0 + 0.5f - 0.5f * (float)g.nx, Y0 = (float)ty0 + 0.5f - 0.5f * (float)g.ny;
-  const float X1 = X0 + (float)(kBwdTile - 1), Y1 = Y0 + (float)(kBwdTile - 1);
+  const float X1 = X0 + (float)(kBwdTileX - 1), Y1 = Y0 + (float)(kBwdTileY - 1);
   const int v = blockIdx.z;
   const size_t col = ((size_t)v * gridDim.x * gridDim.y + (size_t)blockIdx.y * gridDim.x + blockIdx.x) * kBwdWarps + wi;
   PixItem* mypix = pix[wi];
@@ -942,7 +970,7 @@ static cudaError_t table_pass(const DevGeom& g, unsigned char* cnt, unsigned* ba
   const int nr_tile = bwd_rows_per_tile(g);
   const int NT = g.taps;
   const int p_pad = g.P + 2 * (NT - 1) * g.n_seg;
-  dim3 grid((g.nx + kBwdTile - 1) / kBwdTile, (g.ny + kBwdTile - 1) / kBwdTile, g.V);
+  dim3 grid((g.nx + kBwdTileX - 1) / kBwdTileX, (g.ny + kBwdTileY - 1) / kBwdTileY, g.V);
   switch (NT) {
     case 1: k_bwd_items<1, PASS><<<grid, kBwdWarps * 32, 0, s>>>(g, nr_tile, p_pad, bcap, cnt, bad, starts, view_base, items, hdr); break;
     case 2: k_bwd_items<2, PASS><<<grid, kBwdWarps * 32, 0, s>>>(g, nr_tile, p_pad, bcap, cnt, bad, starts, view_base, items, hdr); break;
@@ -957,7 +985,7 @@ cudaError_t backward_table_count(const DevGeom& g, unsigned char* cnt, unsigned*
 
 cudaError_t backward_table_starts(const DevGeom& g, const unsigned char* cnt, unsigned* starts,
                                   unsigned* view_totals, cudaStream_t s) {
-  const size_t cols = (size_t)((g.nx + kBwdTile - 1) / kBwdTile) * ((g.ny + kBwdTile - 1) / kBwdTile) * kBwdWarps;
+  const size_t cols = (size_t)((g.nx + kBwdTileX - 1) / kBwdTileX) * ((g.ny + kBwdTileY - 1) / kBwdTileY) * kBwdWarps;
   k_bwd_table_scan<<<g.V, 1024, 0, s>>>(cnt, cols, starts, view_totals);
   return cudaGetLastError();
 }
@@ -1074,9 +1102,11 @@ cudaError_t launch_forward(const DevGeom& g, int subset, int mode, const FwdArgs
 
 static int bwd_rows_per_tile(const DevGeom& g) {
   // radial rows a tile's footprints can touch: the projection of the tile's pixel centres spans
-  // (kBwdTile - 1)(|c| + |s|) pixels and a footprint |c| + |s| more, at most kBwdTile sqrt(2);
+  // (TX - 1)|c| + (TY - 1)|s| pixels and a footprint |c| + |s| more, at most sqrt(TX^2 + TY^2);
   // the kernel's rounding (ceil - 1 .. floor + 1) adds three rows, one more is margin
-  return (int)floorf(kBwdTile * 1.4143f * g.inv_drp) + 4;
+  const float diag = kBwdTileX == kBwdTileY ? kBwdTileX * 1.4143f
+                                            : sqrtf((float)(kBwdTileX * kBwdTileX + kBwdTileY * kBwdTileY)) * 1.0001f;
+  return (int)floorf(diag * g.inv_drp) + 4;
 }
 
 template <int NT, int ZK, int MODE, bool MASHED>
@@ -1093,14 +1123,15 @@ static cudaError_t bwd_launch(const DevGeom& g, int subset, const BwdArgs& a, cu
   const size_t smem = sw_floats * sizeof(float) + (size_t)kBwdWarps * bcap * (sizeof(float4) + sizeof(int4)) +
                       (size_t)kBwdWarps * g.nr_max * sizeof(PixItem) + (size_t)g.P * sizeof(int);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  if (a.items && (MODE != BWD_UPDATE || MASHED || NT > 3)) return cudaErrorInvalidValue;
+  const int tiles_x = (g.nx + kBwdTileX - 1) / kBwdTileX, tiles_y = (g.ny + kBwdTileY - 1) / kBwdTileY;
   auto kern = a.items ? k_backward<NT, ZK, MODE, MASHED, (MODE == BWD_UPDATE && !MASHED && NT <= 3)>
                       : k_backward<NT, ZK, MODE, MASHED, false>;
-  if (a.items && (MODE != BWD_UPDATE || MASHED || NT > 3)) return cudaErrorInvalidValue;
   {
     cudaError_t e = allow_dynamic_smem(kern, smem);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid((g.nx + kBwdTile - 1) / kBwdTile, (g.ny + kBwdTile - 1) / kBwdTile);
+  dim3 grid(tiles_x, tiles_y);
   kern<<<grid, kBwdWarps * 32, smem, s>>>(g, subset, nr_tile, p_pad, bcap, cpb, a);
   return cudaGetLastError();
 }

@@ -108,7 +108,6 @@ extern "C" int spdhg_autotune(spdhg_ctx* ctx, int reps, int* chosen, void* strea
 
   const DevGeom& g = ctx->dg;
   const int nrows = g.nx > g.ny ? g.nx : g.ny;
-  const int zw = (g.nz + 31) / 32;
   const bool stencil = ctx->params.prior == SPDHG_PRIOR_TV || ctx->params.prior == SPDHG_PRIOR_DTV ||
                        ctx->params.prior == SPDHG_PRIOR_ATV;
   struct Knob {
@@ -137,9 +136,13 @@ extern "C" int spdhg_autotune(spdhg_ctx* ctx, int reps, int* chosen, void* strea
     knobs.push_back(k);
   }
   if (stencil) {
+    Knob vz{SPDHG_TUNE_PRIOR_VZ, false, {1, 2, 4}};
+    knobs.push_back(vz);
+    // columns per block: the launch admits cols x (warps per column) <= 32 at the chosen voxels
+    // per thread; candidates that do not fit are skipped below
     Knob c{SPDHG_TUNE_PRIOR_COLS, false, {}};
     for (int v : {2, 3, 4, 6, 8, 12, 16, 32})
-      if (v * zw <= 32 && v <= g.nx + 1) c.values.push_back(v);
+      if (v <= g.nx + 1) c.values.push_back(v);
     knobs.push_back(c);
     Knob st{SPDHG_TUNE_PRIOR_STAGES, false, {3, 4}};
     knobs.push_back(st);
@@ -155,6 +158,7 @@ extern "C" int spdhg_autotune(spdhg_ctx* ctx, int reps, int* chosen, void* strea
     double best_ms = INFINITY;
     for (int v : k.values) {
       if (spdhg_tune(ctx, k.id, v) != SPDHG_OK) continue;
+      if (!k.forward && !prior_launch_ok(ctx->dg, ctx->params.prior)) continue;
       double ms = 0.0;
       if (int st = time_kernel(ctx, k.forward, reps, s, tm, &ms)) {
         spdhg_tune(ctx, k.id, keep);

@@ -190,10 +190,11 @@ def test_backprojector_item_table_is_bit_identical(sc):
     probs = O.probabilities(sc.n_subsets, _prior("tv"))
     seq = O.sample(77, 40, probs)
     out = []
-    for off in (0, 1):
+    for knobs in ({"bwd_table": 1}, {}):
         with pkg.Context(sc) as ctx:
             upload(ctx, d)
-            ctx.spdhg_tune("bwd_table", off)
+            for k, v in knobs.items():
+                ctx.spdhg_tune(k, v)
             ctx.spdhg_setup(_params(pkg, "tv", 1, False))
             ctx.spdhg_iterate(seq)
             st = {}
@@ -203,6 +204,7 @@ def test_backprojector_item_table_is_bit_identical(sc):
                 st[k] = t
             torch.cuda.synchronize()
             out.append({k: host(v) for k, v in st.items()})
-    for k in out[0]:
-        np.testing.assert_array_equal(out[0][k], out[1][k], err_msg=k)
+    for other in out[1:]:
+        for k in out[0]:
+            np.testing.assert_array_equal(out[0][k], other[k], err_msg=k)
 
