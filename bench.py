@@ -596,7 +596,7 @@ def run_batch(args):
 # learned warm start: U-Net on the 3-D scanner, time to a 1e-3 gap against SPDHG+ from zero
 # ------------------------------------------------------------------------------------------
 
-WS_WORKLOAD = "warmstart-cyl3d-128x128x64-180v128r64p-tv-21subsets-unet16-32-64-128"
+WS_WORKLOAD = "warmstart-cyl3d-oblique-128x128x64-180v128r64p-tv-21subsets-unet16-32-64-128"
 
 
 def unet_flops_per_sample(shape, channels):
@@ -626,7 +626,7 @@ def run_warmstart(args):
     from paper_1808_07150_gb300 import _build_ext, learned, warmstart as W
     torch.cuda.set_device(0)
     _build_ext.build()
-    sc = synth.config_3d()
+    sc = synth.config_3d_oblique()
     k, ref_epochs, max_epochs, group = args.k, 60, 30, 32
     channels = (16, 32, 64, 128)
     alpha = 0.05
@@ -778,7 +778,7 @@ def run_warmstart(args):
 # the paper's comparison: SPDHG (scalar steps) against SPDHG+ (preconditioned), from zero
 # ------------------------------------------------------------------------------------------
 
-PRECOND_WORKLOAD = "precond-cyl3d-128x128x64-180v128r64p-tv-21subsets"
+PRECOND_WORKLOAD = "precond-cyl3d-oblique-128x128x64-180v128r64p-tv-21subsets"
 
 
 def run_precond(args):
@@ -789,7 +789,7 @@ def run_precond(args):
     from paper_1808_07150_gb300 import _build_ext, warmstart as W
     torch.cuda.set_device(0)
     _build_ext.build()
-    sc = synth.config_3d()
+    sc = synth.config_3d_oblique()
     n_prob, max_plus, max_plain, ref_epochs = 8, 30, 120, 120
 
     def to_dev(a):
@@ -850,7 +850,7 @@ def run_precond(args):
 # the paper's OSEM comparison (Sec. 1.3): MLEM, OSEM and SPDHG+ without a prior on the 3-D scanner
 # ------------------------------------------------------------------------------------------
 
-OSEM_WORKLOAD = "osem-cyl3d-128x128x64-180v128r64p-ml-21subsets"
+OSEM_WORKLOAD = "osem-cyl3d-oblique-128x128x64-180v128r64p-ml-21subsets"
 
 
 def run_osem(args):
@@ -868,7 +868,7 @@ def run_osem(args):
     from paper_1808_07150_gb300 import _build_ext
     torch.cuda.set_device(0)
     _build_ext.build()
-    sc = synth.config_3d()
+    sc = synth.config_3d_oblique()
     d = synth.make_problem(sc, SEED, counts=3e7, bg_frac=0.1, with_mult=True, with_side=False, n_ellipsoids=8)
 
     def to_dev(a):
@@ -928,7 +928,7 @@ def _psnr_summary(rep, thresholds):
 # per-configuration figures: GPU ms per epoch and time to a 1e-3 gap, the oracle's time per epoch
 # ------------------------------------------------------------------------------------------
 
-CONFIGS_WORKLOAD = "configs-2d-64x64-10subsets-tv0.1/3d-128x128x64-21subsets-tv0.05"
+CONFIGS_WORKLOAD = "configs-2d-64x64-10subsets-tv0.1/3d-oblique-128x128x64-21subsets-tv0.05"
 
 
 def _oracle_epoch_seconds(cfg, n_iter):
@@ -938,7 +938,7 @@ def _oracle_epoch_seconds(cfg, n_iter):
     import synth
     from oracle import algorithms as O
     oracle.build()
-    sc = synth.config_2d() if cfg == "2d" else synth.config_3d()
+    sc = synth.config_2d() if cfg == "2d" else synth.config_3d_oblique()
     alpha = 0.1 if cfg == "2d" else 0.05
     d = synth.make_problem(sc, SEED, counts=1e5 if cfg == "2d" else 3e7, bg_frac=0.05 if cfg == "2d" else 0.1,
                            with_mult=False)
@@ -970,7 +970,7 @@ def run_configs(args):
     _build_ext.build()
     res = {}
     for cfg, sc, alpha, counts, bg, n_or in (("2d", synth.config_2d(), 0.1, 1e5, 0.05, 200),
-                                             ("3d", synth.config_3d(), 0.05, 3e7, 0.1, 8)):
+                                             ("3d", synth.config_3d_oblique(), 0.05, 3e7, 0.1, 8)):
         d = synth.make_problem(sc, SEED, counts=counts, bg_frac=bg, with_mult=False)
         with pkg.Context(sc) as ctx:
             ctx.spdhg_set_data(torch.from_numpy(d["b"].ravel()).cuda(), torch.from_numpy(d["r"].ravel()).cuda())

@@ -156,6 +156,9 @@ typedef struct {
  * transaxial pixel, or when a segment has more than 32 components.  *out receives the context
  * (NULL on failure). */
 int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out);
+/* The same call under the name of the problem set-up's first step (the scanner geometry that
+ * defines the projection P of Sec. 1.2). */
+int spdhg_create_geometry(const spdhg_geometry* geom, spdhg_ctx** out);
 
 /* Releases every device buffer of the context.  NULL is accepted. */
 void spdhg_destroy(spdhg_ctx* ctx);
@@ -303,6 +306,14 @@ enum { SPDHG_TUNE_PRIOR_COLS = 0,   /* prior kernel: voxel columns per block, in
 /* Sets one launch-shape knob of the context (value 0: default).  Out-of-range values are rejected
  * with SPDHG_ERR_ARG. */
 int spdhg_tune(spdhg_ctx* ctx, int knob, int value);
+
+/* Device-memory limit of the context, in bytes (0: none, the default).  Every device allocation
+ * of the context (data, state, scratch, the backprojector's item table) is charged to it; one
+ * that would exceed it fails as the driver's own would: the call returns SPDHG_ERR_OOM, the
+ * context stays valid and keeps what it already holds (the item table, an optional cache, is
+ * skipped instead).  A limit below what the context already holds applies to later
+ * allocations only.  *used (may be NULL) receives the bytes the context holds now. */
+int spdhg_set_memory_limit(spdhg_ctx* ctx, uint64_t limit_bytes, uint64_t* used);
 
 /* Picks the launch-shape knobs of the context by measurement: for each knob in turn, every
  * admissible value is timed (CUDA events on `stream`: best of three trials of `reps` launches,

@@ -191,6 +191,12 @@ class Context:
         code = _capi.TUNE[knob] if isinstance(knob, str) else int(knob)
         self._check(_capi.lib().spdhg_tune(self.h, code, int(value)))
 
+    def spdhg_set_memory_limit(self, limit_bytes):
+        """Device-memory limit of the context in bytes (0: none); returns the bytes it holds now."""
+        used = ctypes.c_uint64(0)
+        self._check(_capi.lib().spdhg_set_memory_limit(self.h, int(limit_bytes), ctypes.byref(used)))
+        return int(used.value)
+
     def spdhg_profile(self, enable=True):
         self._check(_capi.lib().spdhg_profile(self.h, int(bool(enable))))
 

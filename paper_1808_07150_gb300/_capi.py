@@ -22,11 +22,12 @@ SUBSETS = {"views": 0, "bins": 1}
 STATE = {"x": 0, "z": 1, "T": 2, "y": 3, "q": 4, "sigma": 5, "w": 6, "zw": 7, "q2": 8}
 
 _EXPORTS = [
-    "spdhg_create", "spdhg_destroy", "spdhg_last_error", "spdhg_sizes", "spdhg_set_data",
+    "spdhg_create", "spdhg_create_geometry", "spdhg_destroy", "spdhg_last_error", "spdhg_sizes", "spdhg_set_data",
     "spdhg_project", "spdhg_backproject", "spdhg_setup", "spdhg_iterate", "spdhg_get",
     "spdhg_objective", "spdhg_probabilities", "spdhg_sample", "spdhg_run", "spdhg_profile",
     "spdhg_profile_read", "spdhg_backproject_noalloc", "spdhg_tune", "spdhg_autotune",
     "spdhg_run_batch", "spdhg_set", "spdhg_save_state", "spdhg_load_state", "spdhg_psnr", "spdhg_osem",
+    "spdhg_set_memory_limit",
     "unet_gemm", "unet_device_error", "unet_create", "unet_destroy", "unet_last_error", "unet_num_params",
     "unet_set_params", "unet_init", "unet_get_params", "unet_get_grads", "unet_forward", "unet_backward", "unet_adam_step",
 ]
@@ -97,6 +98,7 @@ def lib():
         P = ctypes.POINTER
         sig = {
             "spdhg_create": ([P(Geometry), P(vp)], i32),
+            "spdhg_create_geometry": ([P(Geometry), P(vp)], i32),
             "spdhg_destroy": ([vp], None),
             "spdhg_last_error": ([vp], ctypes.c_char_p),
             "spdhg_sizes": ([vp, P(i64), P(i64), P(i32)], i32),
@@ -117,6 +119,7 @@ def lib():
             "spdhg_profile_read": ([vp, P(dp), P(i64), i32], i32),
             "spdhg_backproject_noalloc": ([vp, vp, vp, i32, vp], i32),
             "spdhg_tune": ([vp, i32, i32], i32),
+            "spdhg_set_memory_limit": ([vp, u64, P(u64)], i32),
             "spdhg_autotune": ([vp, i32, P(i32), vp], i32),
             "spdhg_run_batch": ([P(vp), P(Params), P(vp), i32, i32, P(Report), vp], i32),
             "spdhg_psnr": ([vp, vp, vp, i32, P(dp), vp], i32),

@@ -15,6 +15,29 @@
 
 using namespace spdhg;
 
+// Device allocations of a context are charged to its memory limit (spdhg_set_memory_limit): one
+// that would take the context past the limit fails as an out-of-memory error, as the driver's
+// own would, and leaves the context usable.
+cudaError_t spdhg::ctx_malloc(spdhg_ctx* ctx, void** p, size_t bytes) {
+  if (ctx->mem_limit && ctx->mem_used + bytes > ctx->mem_limit) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) {
+    ctx->mem_used += bytes;
+    ctx->mem_size[*p] = bytes;
+  }
+  return e;
+}
+
+void spdhg::ctx_free(spdhg_ctx* ctx, void* p) {
+  if (!p) return;
+  auto it = ctx->mem_size.find(p);
+  if (it != ctx->mem_size.end()) {
+    ctx->mem_used -= it->second;
+    ctx->mem_size.erase(it);
+  }
+  cudaFree(p);
+}
+
 namespace {
 
 int fail(spdhg_ctx* c, int code, const std::string& msg) {
@@ -31,9 +54,9 @@ int fail(spdhg_ctx* c, int code, const std::string& msg) {
   } while (0)
 
 template <class T>
-cudaError_t dalloc(T** p, size_t n) {
+cudaError_t dalloc(spdhg_ctx* ctx, T** p, size_t n) {
   if (*p) return cudaSuccess;
-  return cudaMalloc((void**)p, n * sizeof(T) + 16);
+  return ctx_malloc(ctx, (void**)p, n * sizeof(T) + 16);
 }
 
 __global__ void k_fill(float* p, int64_t n, float v) {
@@ -170,18 +193,18 @@ int prepare_forward(spdhg_ctx* ctx, int subset, FwdArgs& a, cudaStream_t s) {
   const size_t need = lines * split * ctx->dg.P;
   if (need > ctx->fwd_part_cap) {
     ++ctx->graph_gen;  // captured iterations hold the old address
-    if (ctx->fwd_part) cudaFree(ctx->fwd_part);
+    ctx_free(ctx, ctx->fwd_part);
     ctx->fwd_part = nullptr;
     ctx->fwd_part_cap = 0;
-    CK(cudaMalloc(&ctx->fwd_part, need * sizeof(float)));
+    CK(ctx_malloc(ctx, (void**)&ctx->fwd_part, need * sizeof(float)));
     ctx->fwd_part_cap = need;
   }
   if (tickets > ctx->fwd_ticket_cap) {
     ++ctx->graph_gen;
-    if (ctx->fwd_tickets) cudaFree(ctx->fwd_tickets);
+    ctx_free(ctx, ctx->fwd_tickets);
     ctx->fwd_tickets = nullptr;
     ctx->fwd_ticket_cap = 0;
-    CK(cudaMalloc(&ctx->fwd_tickets, tickets * sizeof(unsigned)));
+    CK(ctx_malloc(ctx, (void**)&ctx->fwd_tickets, tickets * sizeof(unsigned)));
     CK(cudaMemsetAsync(ctx->fwd_tickets, 0, tickets * sizeof(unsigned), s));
     ctx->fwd_ticket_cap = tickets;
   }
@@ -371,14 +394,14 @@ static int build_bwd_table(spdhg_ctx* ctx, cudaStream_t s) {
   unsigned *bad = nullptr, *starts = nullptr, *totals = nullptr;
   int status = SPDHG_OK;
   auto release = [&]() {
-    if (cnt) cudaFree(cnt);
-    if (bad) cudaFree(bad);
-    if (starts) cudaFree(starts);
-    if (totals) cudaFree(totals);
+    ctx_free(ctx, cnt);
+    ctx_free(ctx, bad);
+    ctx_free(ctx, starts);
+    ctx_free(ctx, totals);
   };
-  if (cudaMalloc(&cnt, V * cols) != cudaSuccess || cudaMalloc(&bad, sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&starts, V * cols * sizeof(unsigned)) != cudaSuccess ||
-      cudaMalloc(&totals, V * sizeof(unsigned)) != cudaSuccess) {
+  if (ctx_malloc(ctx, (void**)&cnt, V * cols) != cudaSuccess || ctx_malloc(ctx, (void**)&bad, sizeof(unsigned)) != cudaSuccess ||
+      ctx_malloc(ctx, (void**)&starts, V * cols * sizeof(unsigned)) != cudaSuccess ||
+      ctx_malloc(ctx, (void**)&totals, V * sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     release();
     return SPDHG_OK;  // no room for the table: the kernel computes the items
@@ -404,15 +427,16 @@ static int build_bwd_table(spdhg_ctx* ctx, cudaStream_t s) {
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   const size_t need = (size_t)total * sizeof(float4) + V * cols * sizeof(int2);
-  if (hbad || total >= (1ull << 32) || need > free_b / 10 * 4) {
+  if (hbad || total >= (1ull << 32) || need > free_b / 10 * 4 ||
+      (ctx->mem_limit && ctx->mem_used + need > ctx->mem_limit)) {
     release();
     return SPDHG_OK;
   }
-  if (cudaMalloc(&ctx->bwd_items, (size_t)total * sizeof(float4) + 16) != cudaSuccess ||
-      cudaMalloc(&ctx->bwd_hdr, V * cols * sizeof(int2)) != cudaSuccess) {
+  if (ctx_malloc(ctx, (void**)&ctx->bwd_items, (size_t)total * sizeof(float4) + 16) != cudaSuccess ||
+      ctx_malloc(ctx, (void**)&ctx->bwd_hdr, V * cols * sizeof(int2)) != cudaSuccess) {
     cudaGetLastError();
-    if (ctx->bwd_items) cudaFree(ctx->bwd_items);
-    if (ctx->bwd_hdr) cudaFree(ctx->bwd_hdr);
+    ctx_free(ctx, ctx->bwd_items);
+    ctx_free(ctx, ctx->bwd_hdr);
     ctx->bwd_items = nullptr;
     ctx->bwd_hdr = nullptr;
     release();
@@ -430,8 +454,8 @@ static int build_bwd_table(spdhg_ctx* ctx, cudaStream_t s) {
 
 // Drops the table (a knob changed); the next spdhg_setup decides again.
 static void drop_bwd_table(spdhg_ctx* ctx) {
-  if (ctx->bwd_items) cudaFree(ctx->bwd_items);
-  if (ctx->bwd_hdr) cudaFree(ctx->bwd_hdr);
+  ctx_free(ctx, ctx->bwd_items);
+  ctx_free(ctx, ctx->bwd_hdr);
   ctx->bwd_items = nullptr;
   ctx->bwd_hdr = nullptr;
   ctx->bwd_table = -1;
@@ -453,6 +477,8 @@ int spdhg::prepare_all_forward(spdhg_ctx* ctx, cudaStream_t s) {
 }
 
 extern "C" {
+
+int spdhg_create_geometry(const spdhg_geometry* geom, spdhg_ctx** out) { return spdhg_create(geom, out); }
 
 int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   if (!out) return SPDHG_ERR_ARG;
@@ -642,20 +668,20 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
     return e == cudaErrorMemoryAllocation ? SPDHG_ERR_OOM : SPDHG_ERR_CUDA;
   };
   cudaError_t e;
-  if ((e = cudaMalloc(&ctx->d_view, sizeof(float4) * V)) != cudaSuccess) return cleanup_fail(e);
-  if ((e = cudaMalloc(&ctx->d_rad, sizeof(float4) * R)) != cudaSuccess) return cleanup_fail(e);
-  if ((e = cudaMalloc(&ctx->d_rs, sizeof(float4) * R * C)) != cudaSuccess) return cleanup_fail(e);
-  if ((e = cudaMalloc(&ctx->d_comp, sizeof(CompDev) * C)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = ctx_malloc(ctx, (void**)&ctx->d_view, sizeof(float4) * V)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = ctx_malloc(ctx, (void**)&ctx->d_rad, sizeof(float4) * R)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = ctx_malloc(ctx, (void**)&ctx->d_rs, sizeof(float4) * R * C)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = ctx_malloc(ctx, (void**)&ctx->d_comp, sizeof(CompDev) * C)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_comp, comp.data(), sizeof(CompDev) * C, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
-  if ((e = cudaMalloc(&ctx->d_seg, sizeof(SegDev) * S)) != cudaSuccess) return cleanup_fail(e);
-  if ((e = cudaMalloc(&ctx->d_plane_seg, sizeof(int) * P)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = ctx_malloc(ctx, (void**)&ctx->d_seg, sizeof(SegDev) * S)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = ctx_malloc(ctx, (void**)&ctx->d_plane_seg, sizeof(int) * P)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_view, view.data(), sizeof(float4) * V, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_rad, rad.data(), sizeof(float4) * R, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_rs, rs.data(), sizeof(float4) * R * C, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_seg, seg.data(), sizeof(SegDev) * S, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_plane_seg, plane_seg.data(), sizeof(int) * P, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
-  if ((e = cudaMalloc(&ctx->d_runs, sizeof(int2) * runs.size())) != cudaSuccess) return cleanup_fail(e);
-  if ((e = cudaMalloc(&ctx->d_view_inv, sizeof(float2) * V)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = ctx_malloc(ctx, (void**)&ctx->d_runs, sizeof(int2) * runs.size())) != cudaSuccess) return cleanup_fail(e);
+  if ((e = ctx_malloc(ctx, (void**)&ctx->d_view_inv, sizeof(float2) * V)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_view_inv, view_inv.data(), sizeof(float2) * V, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_runs, runs.data(), sizeof(int2) * runs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
 
@@ -707,8 +733,7 @@ void spdhg_destroy(spdhg_ctx* ctx) {
                   ctx->x[0], ctx->x[1], ctx->z, ctx->T, ctx->y, ctx->sigma, ctx->wdy, ctx->q[0], ctx->q[1],
                   ctx->w[0], ctx->w[1], ctx->zw, ctx->q2[0], ctx->q2[1], ctx->tgv_b, ctx->tmp_sino, ctx->tmp_img, ctx->tmp_img2, ctx->em_sens, ctx->bwd_items, ctx->bwd_hdr, ctx->fwd_part, ctx->fwd_tickets,
                   ctx->red, ctx->red_out};
-  for (void* p : ptrs)
-    if (p) cudaFree(p);
+  for (void* p : ptrs) ctx_free(ctx, p);
   for (auto& r : ctx->prof_pending) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -733,21 +758,21 @@ int spdhg_set_data(spdhg_ctx* ctx, const float* b, const float* r, const float* 
   if (!ctx) return SPDHG_ERR_ARG;
   if (!b || !r || (where != SPDHG_WHERE_HOST && where != SPDHG_WHERE_DEVICE)) return fail(ctx, SPDHG_ERR_ARG, "b and r are required");
   if (int st = check_device(ctx)) return st;
-  CK(dalloc(&ctx->b, ctx->M));
-  CK(dalloc(&ctx->r, ctx->M));
-  CK(dalloc(&ctx->red, 2048));
-  CK(dalloc(&ctx->red_out, 8));
+  CK(dalloc(ctx, &ctx->b, ctx->M));
+  CK(dalloc(ctx, &ctx->r, ctx->M));
+  CK(dalloc(ctx, &ctx->red, 2048));
+  CK(dalloc(ctx, &ctx->red_out, 8));
   cudaStream_t s = 0;
   if (int st = copy_in(ctx, ctx->b, b, ctx->M, where, s)) return st;
   if (int st = copy_in(ctx, ctx->r, r, ctx->M, where, s)) return st;
   ctx->has_mult = mult != nullptr;
   if (mult) {
-    CK(dalloc(&ctx->mult, ctx->M));
+    CK(dalloc(ctx, &ctx->mult, ctx->M));
     if (int st = copy_in(ctx, ctx->mult, mult, ctx->M, where, s)) return st;
   }
   ctx->has_side = side != nullptr;
   if (side) {
-    CK(dalloc(&ctx->side, ctx->N));
+    CK(dalloc(ctx, &ctx->side, ctx->N));
     if (int st = copy_in(ctx, ctx->side, side, ctx->N, where, s)) return st;
   }
   unsigned long long* bad = reinterpret_cast<unsigned long long*>(ctx->red_out);
@@ -793,10 +818,10 @@ int spdhg_backproject(spdhg_ctx* ctx, const float* y, float* x, int subset, void
   // subset -1 uses a full-size scratch sinogram
   float* w = nullptr;
   if (subset < 0) {
-    CK(dalloc(&ctx->tmp_sino, ctx->M));
+    CK(dalloc(ctx, &ctx->tmp_sino, ctx->M));
     w = ctx->tmp_sino;
   } else {
-    CK(dalloc(&ctx->wdy, ctx->max_subset_bins));
+    CK(dalloc(ctx, &ctx->wdy, ctx->max_subset_bins));
     w = ctx->wdy;
   }
   CK(launch_gather_subset(ctx->dg, subset, y, ctx->has_mult ? ctx->mult : nullptr, w, s));
@@ -851,25 +876,25 @@ int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int
   const int64_t N = ctx->N, M = ctx->M;
   const int m = ctx->geom.n_subsets;
 
-  CK(dalloc(&ctx->x[0], N));
-  CK(dalloc(&ctx->x[1], N));
-  CK(dalloc(&ctx->z, N));
-  CK(dalloc(&ctx->T, N));
-  CK(dalloc(&ctx->y, M));
-  CK(dalloc(&ctx->sigma, M));
-  CK(dalloc(&ctx->wdy, ctx->max_subset_bins));
+  CK(dalloc(ctx, &ctx->x[0], N));
+  CK(dalloc(ctx, &ctx->x[1], N));
+  CK(dalloc(ctx, &ctx->z, N));
+  CK(dalloc(ctx, &ctx->T, N));
+  CK(dalloc(ctx, &ctx->y, M));
+  CK(dalloc(ctx, &ctx->sigma, M));
+  CK(dalloc(ctx, &ctx->wdy, ctx->max_subset_bins));
   const bool tgv = p.prior == SPDHG_PRIOR_TGV;
   if (p.prior != SPDHG_PRIOR_NONE) {
-    CK(dalloc(&ctx->q[0], 3 * N));
-    CK(dalloc(&ctx->q[1], 3 * N));
+    CK(dalloc(ctx, &ctx->q[0], 3 * N));
+    CK(dalloc(ctx, &ctx->q[1], 3 * N));
   }
   if (tgv) {
-    CK(dalloc(&ctx->w[0], 3 * N));
-    CK(dalloc(&ctx->w[1], 3 * N));
-    CK(dalloc(&ctx->zw, 3 * N));
-    CK(dalloc(&ctx->tgv_b, 6 * N));
-    CK(dalloc(&ctx->q2[0], 6 * N));
-    CK(dalloc(&ctx->q2[1], 6 * N));
+    CK(dalloc(ctx, &ctx->w[0], 3 * N));
+    CK(dalloc(ctx, &ctx->w[1], 3 * N));
+    CK(dalloc(ctx, &ctx->zw, 3 * N));
+    CK(dalloc(ctx, &ctx->tgv_b, 6 * N));
+    CK(dalloc(ctx, &ctx->q2[0], 6 * N));
+    CK(dalloc(ctx, &ctx->q2[1], 6 * N));
   }
 
   if (p.sampling == SPDHG_SAMPLING_CUSTOM) {
@@ -894,8 +919,8 @@ int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int
   // (gamma ||P_i||), with ||P_i|| by power iteration
   std::vector<double> norms;
   if (!p.precond) {
-    CK(dalloc(&ctx->tmp_sino, M));
-    CK(dalloc(&ctx->tmp_img, N));
+    CK(dalloc(ctx, &ctx->tmp_sino, M));
+    CK(dalloc(ctx, &ctx->tmp_img, N));
     double t_data = INFINITY;
     for (int i = 0; i < m; ++i) {
       double nrm = 0.0;
@@ -939,7 +964,7 @@ int spdhg_setup(spdhg_ctx* ctx, const spdhg_params* params, const float* x0, int
   if (!p.precond && ctx->dg.bins) {
     std::vector<float> sig_i(m);
     for (int i = 0; i < m; ++i) sig_i[i] = norms[i] > 0.0 ? (float)(p.gamma * p.rho / norms[i]) : 0.f;
-    CK(dalloc(&ctx->tmp_img, N));  // m <= N floats of per-subset steps
+    CK(dalloc(ctx, &ctx->tmp_img, N));  // m <= N floats of per-subset steps
     if (m > N) return fail(ctx, SPDHG_ERR_UNSUPPORTED, "more bin subsets than voxels");
     CK(cudaMemcpyAsync(ctx->tmp_img, sig_i.data(), m * sizeof(float), cudaMemcpyHostToDevice, s));
     k_fill_bins<<<grid_for(M), 256, 0, s>>>(ctx->sigma, M, m, ctx->tmp_img);
@@ -1098,13 +1123,13 @@ int spdhg_objective(spdhg_ctx* ctx, const float* x, int where, double out[3], vo
   if (!ctx->has_data) return fail(ctx, SPDHG_ERR_STATE, "no data");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t N = ctx->N, M = ctx->M;
-  CK(dalloc(&ctx->tmp_sino, M));
+  CK(dalloc(ctx, &ctx->tmp_sino, M));
   const float* xd = x;
   if (!x) {
     if (!ctx->is_setup) return fail(ctx, SPDHG_ERR_STATE, "no iterate before spdhg_setup");
     xd = ctx->x[ctx->xcur];
   } else if (where == SPDHG_WHERE_HOST) {
-    CK(dalloc(&ctx->tmp_img, N));
+    CK(dalloc(ctx, &ctx->tmp_img, N));
     CK(cudaMemcpyAsync(ctx->tmp_img, x, N * sizeof(float),
                        where == SPDHG_WHERE_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     xd = ctx->tmp_img;
@@ -1147,12 +1172,12 @@ int spdhg_psnr(spdhg_ctx* ctx, const float* x, const float* x_star, int where, d
     if (!ctx->is_setup) return fail(ctx, SPDHG_ERR_STATE, "no iterate before spdhg_setup");
     xd = ctx->x[ctx->xcur];
   } else if (where == SPDHG_WHERE_HOST) {
-    CK(dalloc(&ctx->tmp_img2, N));
+    CK(dalloc(ctx, &ctx->tmp_img2, N));
     CK(cudaMemcpyAsync(ctx->tmp_img2, x, N * sizeof(float), cudaMemcpyHostToDevice, s));
     xd = ctx->tmp_img2;
   }
   if (where == SPDHG_WHERE_HOST) {
-    CK(dalloc(&ctx->tmp_img, N));
+    CK(dalloc(ctx, &ctx->tmp_img, N));
     CK(cudaMemcpyAsync(ctx->tmp_img, x_star, N * sizeof(float), cudaMemcpyHostToDevice, s));
     xs = ctx->tmp_img;
   }
@@ -1192,7 +1217,7 @@ int spdhg::runlog_begin(spdhg_ctx* ctx, const spdhg_params& p, spdhg_report* rep
   }
   if (target) {
     // Psi(0): the zero image, for the normaliser of every run (warm starts included)
-    CK(dalloc(&ctx->tmp_img, ctx->N));
+    CK(dalloc(ctx, &ctx->tmp_img, ctx->N));
     CK(cudaMemsetAsync(ctx->tmp_img, 0, ctx->N * sizeof(float), s));
     double o[3];
     if (int st = spdhg_objective(ctx, ctx->tmp_img, SPDHG_WHERE_DEVICE, o, s)) return st;
@@ -1291,21 +1316,21 @@ int spdhg_osem(spdhg_ctx* ctx, const spdhg_params* params, int mlem, float* x_in
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t N = ctx->N;
   const int m = mlem ? 1 : ctx->geom.n_subsets;
-  CK(dalloc(&ctx->x[0], N));
-  CK(dalloc(&ctx->x[1], N));
-  CK(dalloc(&ctx->wdy, mlem ? ctx->M : ctx->max_subset_bins));
+  CK(dalloc(ctx, &ctx->x[0], N));
+  CK(dalloc(ctx, &ctx->x[1], N));
+  CK(dalloc(ctx, &ctx->wdy, mlem ? ctx->M : ctx->max_subset_bins));
   if (mlem && ctx->max_subset_bins < ctx->M) {
     // MLEM needs a full-size ratio sinogram
-    CK(dalloc(&ctx->tmp_sino, ctx->M));
+    CK(dalloc(ctx, &ctx->tmp_sino, ctx->M));
   }
   float* ratio = (mlem && ctx->max_subset_bins < ctx->M) ? ctx->tmp_sino : ctx->wdy;
   // sensitivity images P_i^T 1 (Eq. EQU:OSEM), or P^T 1 (Eq. EQU:MLEM)
   const int kind = mlem ? 1 : 0;
   if (ctx->em_sens_kind != kind) {
-    if (ctx->em_sens) cudaFree(ctx->em_sens);
+    ctx_free(ctx, ctx->em_sens);
     ctx->em_sens = nullptr;
     ctx->em_sens_kind = -1;
-    CK(cudaMalloc(&ctx->em_sens, (size_t)m * N * sizeof(float)));
+    CK(ctx_malloc(ctx, (void**)&ctx->em_sens, (size_t)m * N * sizeof(float)));
     for (int i = 0; i < m; ++i) {
       const int sub = mlem ? -1 : i;
       CK(launch_gather_subset(ctx->dg, sub, nullptr, ctx->has_mult ? ctx->mult : nullptr, ratio, s));
@@ -1383,6 +1408,13 @@ int spdhg_osem(spdhg_ctx* ctx, const spdhg_params* params, int mlem, float* x_in
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return status;
+}
+
+int spdhg_set_memory_limit(spdhg_ctx* ctx, uint64_t limit_bytes, uint64_t* used) {
+  if (!ctx) return SPDHG_ERR_ARG;
+  ctx->mem_limit = (size_t)limit_bytes;
+  if (used) *used = ctx->mem_used;
+  return SPDHG_OK;
 }
 
 int spdhg_tune(spdhg_ctx* ctx, int knob, int value) {

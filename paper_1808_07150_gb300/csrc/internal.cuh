@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/spdhg.h"
@@ -236,6 +237,10 @@ int runlog_begin(spdhg_ctx* ctx, const spdhg_params& p, spdhg_report* rep, RunLo
 int runlog_epoch(spdhg_ctx* ctx, const spdhg_params& p, spdhg_report* rep, RunLog& L, int e, double epoch_ms,
                  cudaStream_t s);
 
+// device allocations of a context, charged to its memory limit (cudaErrorMemoryAllocation past it)
+cudaError_t ctx_malloc(spdhg_ctx* ctx, void** p, size_t bytes);
+void ctx_free(spdhg_ctx* ctx, void* p);
+
 }  // namespace spdhg
 
 // The opaque context of the C ABI.
@@ -310,4 +315,7 @@ struct spdhg_ctx {
   spdhg::GraphCache* gcache = nullptr;
   uint64_t graph_gen = 0;
   std::vector<double> graph_sig;
+  // device memory the context holds, and its limit (0: none)
+  size_t mem_used = 0, mem_limit = 0;
+  std::unordered_map<void*, size_t> mem_size;
 };

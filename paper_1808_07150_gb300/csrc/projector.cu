@@ -688,9 +688,14 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? kBwdBlocksPerSM : kB
       for (int it = lane; it < n; it += 32) {
         const float4 e = a.items[(size_t)(unsigned)h.x + it];
         const unsigned pk = __float_as_uint(e.w);
-        const int gi = (int)(pk >> 25);
+        const int idx = (int)(pk >> 25);
         myL[it] = make_float4(e.x, e.y, e.z, 0.f);
-        myM[it] = make_int4((int)(pk & 0xFFFFu), (int)((pk >> 16) & 0x1FFu) - 256, g.seg[gi].n + PAD, 0);
+        if constexpr (MASHED) {
+          const CompDev cd = g.comp[idx];
+          myM[it] = make_int4((int)(pk & 0xFFFFu), (int)((pk >> 16) & 0x1FFu) - 256, cd.qhi - cd.qlo, cd.smask);
+        } else {
+          myM[it] = make_int4((int)(pk & 0xFFFFu), (int)((pk >> 16) & 0x1FFu) - 256, g.seg[idx].n + PAD, 0);
+        }
       }
     }
     // 2. footprint pairs of this warp's column (overlaps the copy)
@@ -897,12 +902,16 @@ __global__ void __launch_bounds__(kBwdWarps * 32) k_bwd_items(DevGeom g, int nr_
       const int j0 = segment_taps<NT>(g, Q.r, ci, Q.I, Lk);
       int nt = NT;
       while (nt > 1 && Lk[nt - 1] == 0.f) --nt;
-      const int gi = g.comp[ci].seg;
+      const CompDev cd = g.comp[ci];
+      const int gi = cd.seg;
       const SegDev sd = g.seg[gi];
       const int x = (Q.r - r_min) * p_pad + sd.p0 + (2 * gi + 1) * PAD + j0;
-      const int jp = j0 + PAD + 256;
-      misfit = misfit || x < 0 || x >= 65536 || jp < 0 || jp >= 512 || gi >= 128;
-      const unsigned packed = ((unsigned)x & 0xFFFFu) | (((unsigned)jp & 0x1FFu) << 16) | ((unsigned)gi << 25);
+      // first tap's offset: to the segment's frame (unmashed) or to the component's first plane
+      // (mashed, whose bound and parity come from the component), and which of the two indexes
+      const int jp = (g.mashed ? j0 - cd.qlo : j0 + PAD) + 256;
+      const int idx = g.mashed ? ci : gi;
+      misfit = misfit || x < 0 || x >= 65536 || jp < 0 || jp >= 512 || idx >= 128;
+      const unsigned packed = ((unsigned)x & 0xFFFFu) | (((unsigned)jp & 0x1FFu) << 16) | ((unsigned)idx << 25);
       It[h] = make_float4(Lk[0], Lk[1], Lk[2], __uint_as_float(packed));
       nt2[h] = nt;
     }
@@ -954,9 +963,11 @@ __global__ void __launch_bounds__(1024) k_bwd_table_scan(const unsigned char* cn
   if (threadIdx.x == 0) totals[v] = (unsigned)total;
 }
 
+// one table record per (pair, component) item of a single batch: mashed geometries qualify when
+// all their components fit in one batch of the backprojector
 bool backward_table_possible(const DevGeom& g) {
   const int max_pairs = (int)floorf(1.4143f * g.inv_drp) + 2;
-  return !g.mashed && !g.bins && g.taps <= 3 && g.nr_max <= kTabMaxPairs && max_pairs * g.n_comp <= kBwdMaxItems;
+  return !g.bins && g.taps <= 3 && g.nr_max <= kTabMaxPairs && max_pairs * g.n_comp <= kBwdMaxItems;
 }
 
 static int bwd_rows_per_tile(const DevGeom& g);
@@ -1123,10 +1134,12 @@ static cudaError_t bwd_launch(const DevGeom& g, int subset, const BwdArgs& a, cu
   const size_t smem = sw_floats * sizeof(float) + (size_t)kBwdWarps * bcap * (sizeof(float4) + sizeof(int4)) +
                       (size_t)kBwdWarps * g.nr_max * sizeof(PixItem) + (size_t)g.P * sizeof(int);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
-  if (a.items && (MODE != BWD_UPDATE || MASHED || NT > 3)) return cudaErrorInvalidValue;
+  // the table holds one batch of items: mashed geometries with more components run without it
+  const bool tab = a.items && MODE == BWD_UPDATE && NT <= 3 && cpb == g.n_comp;
+  if (a.items && (MODE != BWD_UPDATE || NT > 3)) return cudaErrorInvalidValue;
   const int tiles_x = (g.nx + kBwdTileX - 1) / kBwdTileX, tiles_y = (g.ny + kBwdTileY - 1) / kBwdTileY;
-  auto kern = a.items ? k_backward<NT, ZK, MODE, MASHED, (MODE == BWD_UPDATE && !MASHED && NT <= 3)>
-                      : k_backward<NT, ZK, MODE, MASHED, false>;
+  auto kern = tab ? k_backward<NT, ZK, MODE, MASHED, (MODE == BWD_UPDATE && NT <= 3)>
+                  : k_backward<NT, ZK, MODE, MASHED, false>;
   {
     cudaError_t e = allow_dynamic_smem(kern, smem);
     if (e != cudaSuccess) return e;

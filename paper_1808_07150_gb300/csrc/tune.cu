@@ -98,8 +98,8 @@ extern "C" int spdhg_autotune(spdhg_ctx* ctx, int reps, int* chosen, void* strea
     return fail(ctx, SPDHG_ERR_STATE, "current CUDA device differs from the context's device");
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t N = ctx->N, M = ctx->M;
-  if (!ctx->tmp_sino) TCK(cudaMalloc(&ctx->tmp_sino, M * sizeof(float) + 16));
-  if (!ctx->tmp_img) TCK(cudaMalloc(&ctx->tmp_img, N * sizeof(float) + 16));
+  if (!ctx->tmp_sino) TCK(ctx_malloc(ctx, (void**)&ctx->tmp_sino, M * sizeof(float) + 16));
+  if (!ctx->tmp_img) TCK(ctx_malloc(ctx, (void**)&ctx->tmp_img, N * sizeof(float) + 16));
   TCK(cudaMemcpyAsync(ctx->tmp_sino, ctx->y, M * sizeof(float), cudaMemcpyDeviceToDevice, s));
   TCK(cudaMemcpyAsync(ctx->tmp_img, ctx->z, N * sizeof(float), cudaMemcpyDeviceToDevice, s));
   Timer tm;
@@ -155,7 +155,10 @@ extern "C" int spdhg_autotune(spdhg_ctx* ctx, int reps, int* chosen, void* strea
     if (k.values.size() < 2) continue;
     const int keep = g.tune[k.id];
     int best = keep;
+    // the current setting is the one to beat (a candidate list need not hold the built-in choice)
     double best_ms = INFINITY;
+    if (k.forward || prior_launch_ok(ctx->dg, ctx->params.prior))
+      if (int st = time_kernel(ctx, k.forward, reps, s, tm, &best_ms)) return st;
     for (int v : k.values) {
       if (spdhg_tune(ctx, k.id, v) != SPDHG_OK) continue;
       if (!k.forward && !prior_launch_ok(ctx->dg, ctx->params.prior)) continue;

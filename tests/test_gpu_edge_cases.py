@@ -97,3 +97,45 @@ def test_axial_extent_beyond_128_slices():
     d, prob = problem(sc)
     out, st, steps = _run(sc, d, prob, "tv")
     _check(out, st, steps)
+
+
+def test_memory_limit_fails_as_out_of_memory_and_the_context_recovers():
+    """An allocation past the context's memory limit fails with SPDHG_ERR_OOM, as a failed
+    cudaMalloc would, without faulting anything: the context keeps what it holds, and once the
+    limit is lifted the same calls succeed and give the bits of a context that never hit it."""
+    import torch
+    import paper_1808_07150_gb300 as pkg
+    sc = synth.config_2d()
+    d, _ = problem(sc)
+    params = pkg.make_params("tv", alpha=0.1, seed=3)
+    seq = O.sample(11, 20, O.probabilities(sc.n_subsets, O.Prior("tv", alpha=0.1)))
+
+    def state(ctx):
+        x = torch.zeros(sc.n_voxels, device="cuda")
+        ctx.spdhg_get("x", x)
+        torch.cuda.synchronize()
+        return host(x)
+
+    with pkg.Context(sc) as ref:
+        upload(ref, d)
+        ref.spdhg_setup(params)
+        ref.spdhg_iterate(seq)
+        x_ref = state(ref)
+    with pkg.Context(sc) as ctx:
+        held = ctx.spdhg_set_memory_limit(0)
+        assert held > 0                      # the geometry tables
+        ctx.spdhg_set_memory_limit(held + 1024)
+        with pytest.raises(pkg.SpdhgError) as e:
+            upload(ctx, d)
+        assert e.value.code == -3            # SPDHG_ERR_OOM
+        ctx.spdhg_set_memory_limit(0)
+        upload(ctx, d)
+        held = ctx.spdhg_set_memory_limit(0)
+        ctx.spdhg_set_memory_limit(held + 4096)
+        with pytest.raises(pkg.SpdhgError) as e:
+            ctx.spdhg_setup(params)
+        assert e.value.code == -3
+        assert ctx.spdhg_set_memory_limit(0) >= held
+        ctx.spdhg_setup(params)
+        ctx.spdhg_iterate(seq)
+        np.testing.assert_array_equal(state(ctx), x_ref)
