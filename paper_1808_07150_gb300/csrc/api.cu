@@ -635,7 +635,8 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
     split((g.seg_zmid0[k] - loz) / g.vz, seg[k].f_hi, seg[k].f_lo);
     seg[k].c0 = -1;
     seg[k].nc = 0;
-    for (int q = 0; q < g.seg_n[k]; ++q) plane_seg[p0 + q] = k;
+    // the backprojector's staged slot of each plane: segment k's planes follow 2k + 1 frames
+    for (int q = 0; q < g.seg_n[k]; ++q) plane_seg[p0 + q] = p0 + q + (2 * k + 1) * (taps - 1);
     p0 += g.seg_n[k];
   }
   for (int c = 0; c < C; ++c) {
@@ -707,7 +708,7 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   d.rad = ctx->d_rad;
   d.rs = ctx->d_rs;
   d.seg = ctx->d_seg;
-  d.plane_seg = ctx->d_plane_seg;
+  d.stage_pos = ctx->d_plane_seg;
   d.n_runs = (int)runs.size();
   d.runs = ctx->d_runs;
   for (int w = 0; w <= 16; ++w) {

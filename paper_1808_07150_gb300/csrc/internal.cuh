@@ -54,7 +54,7 @@ struct DevGeom {
   const float4* rs;      // per (radial bin, component): kappa_hi, kappa_lo, len_scale, 0
   const SegDev* seg;
   const CompDev* comp;
-  const int* plane_seg;  // plane -> segment
+  const int* stage_pos;  // plane -> its slot in the backprojector's staged rows (frames included)
   int n_runs;            // plane runs of the forward projector: run k = planes [q0, q0 + 32) of one segment
   const int2* runs;      // (segment, q0) per run, segment-major
   int max_part_comps[17];  // forward: most components one block spans, by warps per block

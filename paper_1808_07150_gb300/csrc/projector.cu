@@ -441,7 +441,10 @@ __global__ void __launch_bounds__(512) k_forward(DevGeom g, int subset, int ecap
         const Rec t = tr0[eg + k * egroups];
         const int off = t.off & kOffMask, nt = NT > 1 ? (t.off >> kOffBits) : 1;
         const float* xa = xb + off + qr_[0];
-        const float* xc = xb + off + qr_[1];
+        // the warp's second run is the next 32 planes of the segment: a constant offset.  Lanes
+        // past the segment's last plane read up to 31 slots beyond their column (the next
+        // column, or the tap records after the last buffer) and are never written
+        const float* xc = xa + 32;
         s2 = ffma2_bcast(t.l0, xa[0], xc[0], s2);
         if (NT > 1 && nt > 1) {
           s2 = ffma2_bcast(t.l1, xa[-1], xc[-1], s2);
@@ -614,7 +617,6 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? kBwdBlocksPerSM : kB
   float4* itL = reinterpret_cast<float4*>(sw + ((nr_tile * p_pad + 3) & ~3));  // [warp][icap]
   int4* itM = reinterpret_cast<int4*>(itL + kBwdWarps * icap);
   PixItem* pix = reinterpret_cast<PixItem*>(itM + kBwdWarps * icap);          // [warp][nr_max]
-  int* seg_of = reinterpret_cast<int*>(pix + kBwdWarps * g.nr_max);           // [P]: padded position
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   float4* myL = itL + wi * icap;
   int4* myM = itM + wi * icap;
@@ -631,6 +633,30 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? kBwdBlocksPerSM : kB
   float acc[ZK];
 #pragma unroll
   for (int k = 0; k < ZK; ++k) acc[k] = 0.f;
+  // 1. rows r_min..r_max of view l of the subset -> their slots in the staged rows (each segment's
+  //    planes framed by zeros); the radial rows are those of the whole tile's footprints (its
+  //    extreme pixel centres).  The first view's copies are issued before anything else.
+  auto rows_of = [&](int l, int* rmin) {
+    const float4 cs = g.view[subset_view(g, subset, l)];
+    const float hw = 0.5f * (fabsf(cs.x) + fabsf(cs.z));
+    const float s00 = X0 * cs.x + Y0 * cs.z, s01 = X0 * cs.x + Y1 * cs.z;
+    const float s10 = X1 * cs.x + Y0 * cs.z, s11 = X1 * cs.x + Y1 * cs.z;
+    const float smin = fminf(fminf(s00, s01), fminf(s10, s11)), smax = fmaxf(fmaxf(s00, s01), fmaxf(s10, s11));
+    const int r_min = max(0, (int)ceilf((smin - hw) * g.inv_drp + g.half_R) - 1);
+    *rmin = r_min;
+    return min(g.R - 1, min(r_min + nr_tile - 1, (int)floorf((smax + hw) * g.inv_drp + g.half_R) + 1));
+  };
+  auto stage = [&](int l) {
+    int r_min;
+    const int r_max = rows_of(l, &r_min);
+    const float* src = a.w + ((size_t)l * g.R + r_min) * g.P;
+    const int nr = r_max - r_min + 1;
+    for (int p = threadIdx.x; p < g.P; p += blockDim.x) {
+      const int dst = __ldg(g.stage_pos + p);
+      for (int rr = 0; rr < nr; ++rr) cp_async4(sw + rr * p_pad + dst, src + rr * g.P + p);
+    }
+  };
+  if (nviews > 0) stage(0);
   if constexpr (MODE == BWD_UPDATE) {
     // the epilogue's x, z, T lines of the block's columns are requested into L2 now, so that
     // their DRAM reads overlap the staging and the gather
@@ -644,8 +670,7 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? kBwdBlocksPerSM : kB
       }
     }
   }
-  // padded position of every plane, and the zero frames of the staged rows (written once)
-  for (int p = threadIdx.x; p < g.P; p += blockDim.x) seg_of[p] = p + (2 * g.plane_seg[p] + 1) * PAD;
+  // the zero frames of the staged rows (written once; the copies never touch them)
   if constexpr (PAD > 0) {
     for (int i = threadIdx.x; i < nr_tile * g.n_seg * 2 * PAD; i += blockDim.x) {
       const int rr = i / (g.n_seg * 2 * PAD), rem = i - rr * (g.n_seg * 2 * PAD);
@@ -661,21 +686,9 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? kBwdBlocksPerSM : kB
     const int v = subset_view(g, subset, l);
     const float4 cs = g.view[v];
     const float hw = 0.5f * (fabsf(cs.x) + fabsf(cs.z));
-    // radial rows of the whole tile (footprints of its extreme pixel centres)
-    const float s00 = X0 * cs.x + Y0 * cs.z, s01 = X0 * cs.x + Y1 * cs.z;
-    const float s10 = X1 * cs.x + Y0 * cs.z, s11 = X1 * cs.x + Y1 * cs.z;
-    const float smin = fminf(fminf(s00, s01), fminf(s10, s11)), smax = fmaxf(fmaxf(s00, s01), fmaxf(s10, s11));
-    const int r_min = max(0, (int)ceilf((smin - hw) * g.inv_drp + g.half_R) - 1);
-    const int r_max = min(g.R - 1, min(r_min + nr_tile - 1, (int)floorf((smax + hw) * g.inv_drp + g.half_R) + 1));
-    // 1. stage rows r_min..r_max of this view into their padded slots
-    {
-      const float* src = a.w + ((size_t)l * g.R + r_min) * g.P;
-      const int nr = r_max - r_min + 1;
-      for (int p = threadIdx.x; p < g.P; p += blockDim.x) {
-        const int dst = seg_of[p];
-        for (int rr = 0; rr < nr; ++rr) cp_async4(sw + rr * p_pad + dst, src + rr * g.P + p);
-      }
-    }
+    int r_min;
+    const int r_max = rows_of(l, &r_min);
+    if (l > 0) stage(l);
     int bs[5] = {0, 0, 0, 0, 0};  // bucket b (items with b + 1 taps) spans [bs[b], bs[b + 1])
     if constexpr (TAB) {
       // 2-3. this column's items, in the order the code below computes them, from the table
@@ -1132,7 +1145,7 @@ static cudaError_t bwd_launch(const DevGeom& g, int subset, const BwdArgs& a, cu
   const int p_pad = g.P + 2 * (NT - 1) * g.n_seg;  // each segment framed by NT-1 zeros
   const size_t sw_floats = ((size_t)nr_tile * p_pad + 3) & ~(size_t)3;
   const size_t smem = sw_floats * sizeof(float) + (size_t)kBwdWarps * bcap * (sizeof(float4) + sizeof(int4)) +
-                      (size_t)kBwdWarps * g.nr_max * sizeof(PixItem) + (size_t)g.P * sizeof(int);
+                      (size_t)kBwdWarps * g.nr_max * sizeof(PixItem);
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   // the table holds one batch of items: mashed geometries with more components run without it
   const bool tab = a.items && MODE == BWD_UPDATE && NT <= 3 && cpb == g.n_comp;
