@@ -626,7 +626,7 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   const double loz = -0.5 * g.nz * g.vz;
   std::vector<SegDev> seg(S);
   std::vector<CompDev> comp(C);
-  std::vector<int> plane_seg(P);
+  std::vector<int> stage_pos(P);
   int p0 = 0;
   int fz_lo = taps - 1, fz_stride = g.nz;
   for (int k = 0; k < S; ++k) {
@@ -636,7 +636,7 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
     seg[k].c0 = -1;
     seg[k].nc = 0;
     // the backprojector's staged slot of each plane: segment k's planes follow 2k + 1 frames
-    for (int q = 0; q < g.seg_n[k]; ++q) plane_seg[p0 + q] = p0 + q + (2 * k + 1) * (taps - 1);
+    for (int q = 0; q < g.seg_n[k]; ++q) stage_pos[p0 + q] = p0 + q + (2 * k + 1) * (taps - 1);
     p0 += g.seg_n[k];
   }
   for (int c = 0; c < C; ++c) {
@@ -675,12 +675,12 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   if ((e = ctx_malloc(ctx, (void**)&ctx->d_comp, sizeof(CompDev) * C)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_comp, comp.data(), sizeof(CompDev) * C, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = ctx_malloc(ctx, (void**)&ctx->d_seg, sizeof(SegDev) * S)) != cudaSuccess) return cleanup_fail(e);
-  if ((e = ctx_malloc(ctx, (void**)&ctx->d_plane_seg, sizeof(int) * P)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = ctx_malloc(ctx, (void**)&ctx->d_stage_pos, sizeof(int) * P)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_view, view.data(), sizeof(float4) * V, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_rad, rad.data(), sizeof(float4) * R, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_rs, rs.data(), sizeof(float4) * R * C, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_seg, seg.data(), sizeof(SegDev) * S, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
-  if ((e = cudaMemcpy(ctx->d_plane_seg, plane_seg.data(), sizeof(int) * P, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
+  if ((e = cudaMemcpy(ctx->d_stage_pos, stage_pos.data(), sizeof(int) * P, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
   if ((e = ctx_malloc(ctx, (void**)&ctx->d_runs, sizeof(int2) * runs.size())) != cudaSuccess) return cleanup_fail(e);
   if ((e = ctx_malloc(ctx, (void**)&ctx->d_view_inv, sizeof(float2) * V)) != cudaSuccess) return cleanup_fail(e);
   if ((e = cudaMemcpy(ctx->d_view_inv, view_inv.data(), sizeof(float2) * V, cudaMemcpyHostToDevice)) != cudaSuccess) return cleanup_fail(e);
@@ -708,7 +708,7 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
   d.rad = ctx->d_rad;
   d.rs = ctx->d_rs;
   d.seg = ctx->d_seg;
-  d.stage_pos = ctx->d_plane_seg;
+  d.stage_pos = ctx->d_stage_pos;
   d.n_runs = (int)runs.size();
   d.runs = ctx->d_runs;
   for (int w = 0; w <= 16; ++w) {
@@ -730,7 +730,7 @@ int spdhg_create(const spdhg_geometry* geom, spdhg_ctx** out) {
 
 void spdhg_destroy(spdhg_ctx* ctx) {
   if (!ctx) return;
-  void* ptrs[] = {ctx->d_view, ctx->d_view_inv, ctx->d_rad, ctx->d_rs, ctx->d_runs, ctx->d_seg, ctx->d_comp, ctx->d_plane_seg, ctx->b, ctx->r, ctx->mult, ctx->side,
+  void* ptrs[] = {ctx->d_view, ctx->d_view_inv, ctx->d_rad, ctx->d_rs, ctx->d_runs, ctx->d_seg, ctx->d_comp, ctx->d_stage_pos, ctx->b, ctx->r, ctx->mult, ctx->side,
                   ctx->x[0], ctx->x[1], ctx->z, ctx->T, ctx->y, ctx->sigma, ctx->wdy, ctx->q[0], ctx->q[1],
                   ctx->w[0], ctx->w[1], ctx->zw, ctx->q2[0], ctx->q2[1], ctx->tgv_b, ctx->tmp_sino, ctx->tmp_img, ctx->tmp_img2, ctx->em_sens, ctx->bwd_items, ctx->bwd_hdr, ctx->fwd_part, ctx->fwd_tickets,
                   ctx->red, ctx->red_out};

@@ -261,7 +261,7 @@ struct spdhg_ctx {
   float2* d_view_inv = nullptr;
   spdhg::SegDev* d_seg = nullptr;
   spdhg::CompDev* d_comp = nullptr;
-  int* d_plane_seg = nullptr;
+  int* d_stage_pos = nullptr;
   // data
   float *b = nullptr, *r = nullptr, *mult = nullptr, *side = nullptr;
   bool has_data = false, has_mult = false, has_side = false;
