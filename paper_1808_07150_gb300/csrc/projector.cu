@@ -601,12 +601,16 @@ __device__ __forceinline__ void gather_items(const float* sw, const float4* myL,
 
 // Backprojection.  A block owns a 4 x 4 tile of voxel columns; for each view of the subset it
 // stages the contiguous radial rows w[view][r_min..r_max][0..P) that the tile's footprints
-// touch into shared memory (cp.async, overlapped with the geometry below), each segment's plane
-// run framed by NT-1 zeros so that taps leaving the segment read zeros.  Each warp owns one
-// column: its lanes find the footprint (bin, pixel interval) pairs, compact them with a ballot,
-// compute the axial taps of every (pair, segment) item, and then gather along contiguous plane
-// runs from shared memory, lane = iz mod 32, ZK voxels per lane.  Up to 128 slices (ZK <= 4) four
-// blocks share an SM (32 registers per thread); with eight accumulators per lane, three.
+// touch into shared memory (cp.async, overlapped with the geometry below; the first view's copies
+// are issued before anything else), each segment's plane run framed by NT-1 zeros so that taps
+// leaving the segment read zeros.  Each warp owns one column: its lanes find the footprint (bin,
+// pixel interval) pairs, compact them with a ballot, compute the axial taps of every (pair,
+// segment) item, and then gather along contiguous plane runs from shared memory, lane = iz mod
+// 32, ZK voxels per lane.  With TAB the items, in the same order, are read from the table
+// spdhg_setup builds (k_bwd_items) instead of being computed.  In BWD_UPDATE the epilogue's x, z,
+// T lines are requested into L2 at block start, and after the last view each warp goes on to its
+// epilogue without waiting for the others.  Up to 128 slices (ZK <= 4) four blocks share an SM
+// (32 registers per thread); with eight accumulators per lane, three.
 template <int NT, int ZK, int MODE, bool MASHED, bool TAB>
 __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? kBwdBlocksPerSM : kBwdBlocksPerSM8) k_backward(DevGeom g, int subset, int nr_tile, int p_pad,
                                                              int bcap, int cpb, BwdArgs a) {
@@ -850,8 +854,8 @@ __global__ void __launch_bounds__(kBwdWarps * 32, ZK <= 4 ? kBwdBlocksPerSM : kB
 }
 
 // ---------------------------------------------------------------------------------------
-// tap-item table of the backprojector: the (pair, segment) items of every view, tile and column,
-// computed once by the code the kernel runs and read back by k_backward_tab
+// tap-item table of the backprojector: the (pair, component) items of every view, tile and
+// column, computed once by the code the kernel runs and read back by k_backward<..., TAB>
 // ---------------------------------------------------------------------------------------
 
 constexpr int kTabMaxPairs = 16;  // candidate radial bins per column and view (nr_max <= 16)
